@@ -1,0 +1,219 @@
+/*
+ * ges.h -- C ABI of libges.so, a GB300 (sm_103a) rasterizer for
+ * generalized-exponential splats (GES), forward and backward.
+ *
+ * The method is the GES splatting of DyGASR (Sec. 3.2): each splat i has a
+ * centre x_i, a covariance Sigma = R S S^T R^T (Eq. 4) whose scales are
+ * modulated by phi(beta) (Eq. 6-7), a shape parameter beta (the paper's
+ * epsilon, Eq. 1 and Eq. 3), an opacity and a colour. It is projected to the
+ * image with Sigma' = J W Sigma W^T J^T (Sec. 3.2), evaluated with the falloff
+ * exp(-1/2 Q^(beta/2)) of Eq. 3 (Q the Mahalanobis distance under Sigma'),
+ * and composited front to back, the discrete form of the volume rendering
+ * integral of Eq. 5, into colour, depth (Sec. 3.3, the depth map that mesh
+ * extraction samples), alpha, and the normal n_g* of the flattened splats
+ * (Sec. 3.3, Eq. 10-13).
+ *
+ * Conventions
+ *  - Every pointer argument except `cams`, `cfg` and `count` is a DEVICE
+ *    pointer owned by the caller. The library allocates nothing; it never calls
+ *    cudaMalloc and never frees caller memory.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream), except ges_instance_count and ges_sync_status, which
+ *    synchronise it.
+ *  - Arguments are checked on the host before anything is launched; a bad
+ *    argument returns GES_ERR_INVALID_ARG and launches nothing. A failed launch
+ *    returns GES_ERR_CUDA. Conditions found on the device (instance capacity
+ *    exceeded, non-finite projected values) are recorded in an error word inside
+ *    `proj` and reported by ges_sync_status.
+ *  - Arrays are float32, row-major, C-contiguous. All views of a call are
+ *    concatenated: pixel arrays hold view 0's pixels, then view 1's, etc.
+ *  - The calls are not thread-safe for one `proj` / `bins` pair; distinct
+ *    buffers may be used concurrently on distinct streams.
+ *
+ * Readings where the paper is silent (the full list with reasons is in the
+ * repository's design notes):
+ *  - phi_mode 1 (default): phi(beta) = 2 / (1 + exp(-rho (beta - 2))), so
+ *    phi(2) = 1 and beta = 2 is the 3DGS Gaussian; phi_mode 2 evaluates Eq. 7
+ *    as printed, 2 / (1 + exp(-(rho beta - 2 beta))); phi_mode 0 is phi = 1.
+ *    phi multiplies all three scales.
+ *  - alpha = min(alpha_max, o exp(-1/2 Q^(beta/2))); alpha < alpha_min is
+ *    skipped; the splat that would take transmittance below t_min ends the
+ *    pixel and is not blended. The support used for binning is the exact level
+ *    set Q <= q_cut = (2 ln(o / alpha_min))^(2 / beta).
+ *  - Depth output = sum_i w_i z_i with z the camera-space z (not divided by
+ *    alpha). Normal output = sum_i w_i n_i, n_i the world-space axis of the
+ *    smallest scale turned to face the camera. Colour adds T_final * bg.
+ *  - Colour: sh_degree -1 takes `color` as RGB [N, 3]; degree d in 0..3 takes
+ *    real spherical-harmonic coefficients [N, (d+1)^2, 3] (Condon-Shortley
+ *    phase, ordered by l then m = -l..l) evaluated in the direction from the
+ *    camera centre to the splat, rgb = max(0, sum_k c_k Y_k + 0.5).
+ *  - Pixel (x, y) is sampled at (x + 0.5, y + 0.5).
+ *  - Depth order within a tile: ascending float32 camera depth
+ *    z32 = ((r20 x + r21 y) + r22 z) + t2, each operation rounded to float32,
+ *    ties by entry index (entry = view * N + splat). The same z32 decides the
+ *    near-plane cull (z32 > znear).
+ *  - Tile lists: tile t lists a splat iff the minimum of Q over the rectangle of
+ *    pixel centres of t (clipped to the splat's pixel box) is <= q_cut (1 + 2^-10),
+ *    evaluated in float32 without fused multiply-adds in a fixed operation order.
+ */
+#ifndef GES_H
+#define GES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GES_API __attribute__((visibility("default")))
+#else
+#define GES_API
+#endif
+
+#define GES_ABI_VERSION 1
+#define GES_MAX_VIEWS 32
+
+typedef enum ges_status {
+    GES_OK = 0,
+    GES_ERR_INVALID_ARG = 1, /* host-side check failed; nothing was launched */
+    GES_ERR_CAPACITY = 2,    /* more tile instances than `bins` holds; lists were truncated */
+    GES_ERR_CUDA = 3,        /* a CUDA launch or copy failed */
+    GES_ERR_NUMERIC = 4      /* a visible splat had a non-finite projection; it was culled */
+} ges_status;
+
+/* Pinhole camera. viewmat: row-major 3x4 world-to-camera [R | t]; camera x right,
+ * y down, z forward. Pixel (x, y) maps to u = fx X/Z + cx, v = fy Y/Z + cy. */
+typedef struct ges_camera {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float viewmat[12];
+    float znear;
+} ges_camera;
+
+/* Rasterizer settings. Defaults (the "3DGS standards" the paper keeps, Sec. 4.2):
+ * tile 16x16, batch 256, phi_mode 1, rho 0.1, lowpass 0.3, alpha_min 1/255,
+ * alpha_max 0.99, t_min 1e-4, jac_clamp 1.3. */
+typedef struct ges_config {
+    int32_t tile_w, tile_h; /* 16x16, 8x8 or 32x8 */
+    int32_t batch;          /* splat records staged in shared memory per round: 32..256, multiple of 32 */
+    int32_t sh_degree;      /* -1 (RGB given) or 0..3 */
+    int32_t phi_mode;       /* 0 off, 1 centred (default), 2 as printed in Eq. 7 */
+    float rho;              /* shape strength of Eq. 7 (0.1, Sec. 4.2) */
+    float lowpass;          /* h added to the diagonal of Sigma' */
+    float alpha_min, alpha_max, t_min;
+    float jac_clamp;        /* |X/Z| is clamped to jac_clamp * (W/2)/fx in J (likewise y) */
+    float bg[3];            /* background colour */
+    int32_t persistent;     /* 0: one CTA per tile; 1: persistent CTAs over a longest-first tile queue */
+} ges_config;
+
+/* Number of bytes `proj` must hold for n splats and n_views views:
+ * per (view, splat) a 64-byte render record, a 16-byte binning record and a
+ * 64-byte screen-space gradient accumulator, plus a 256-byte header. */
+GES_API size_t ges_proj_bytes(int32_t n, int32_t n_views);
+
+/* Number of bytes `bins` must hold to bin up to `capacity` tile instances
+ * (splat-tile overlaps) for n splats over the given views and tile shape. */
+GES_API size_t ges_bins_bytes(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                      uint64_t capacity);
+
+/* S1-S4: projection (Eq. 4, Eq. 6-7, Sec. 3.2), GES support (Eq. 3), colour and
+ * normal, tile counts and float32 depth keys, for every (view, splat) entry.
+ * Inputs (device, float32):
+ *   pos_op      [n, 4]  x, y, z, opacity in (0, 1] (already activated)
+ *   lscale_beta [n, 4]  log-scales l1, l2, l3 and beta > 0
+ *   quat        [n, 4]  rotation (w, x, y, z), any non-zero norm
+ *   color       [n, 3] RGB (sh_degree -1) or [n, (d+1)^2, 3] SH coefficients
+ * cams: host array of n_views cameras (1 <= n_views <= GES_MAX_VIEWS).
+ * Writes `proj` (ges_proj_bytes(n, n_views) bytes, 16-byte aligned), and the
+ * total instance count read by ges_instance_count. Clears the error word. */
+GES_API ges_status ges_preprocess(int32_t n, const float *pos_op, const float *lscale_beta, const float *quat,
+                          const float *color, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                          void *proj, size_t proj_bytes, void *stream);
+
+/* Synchronises `stream` and returns in *count the number of tile instances that
+ * the last ges_preprocess on `proj` produced (sum of tiles touched). */
+GES_API ges_status ges_instance_count(const void *proj, size_t proj_bytes, uint64_t *count, void *stream);
+
+/* S5: binning. Sorts entries by float32 depth (stable LSD radix sort), emits one
+ * (global tile, entry) instance per listed tile in depth order, sorts the
+ * instances by tile (stable, so depth order is kept within a tile) and finds
+ * each tile's [start, end) range. With cfg->persistent it also builds the
+ * longest-first tile queue. If the instances exceed the capacity `bins` was
+ * sized for, the lists are truncated and GES_ERR_CAPACITY is recorded. */
+GES_API ges_status ges_bin(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg, void *proj,
+                   size_t proj_bytes, void *bins, size_t bins_bytes, void *stream);
+
+/* S6: forward compositing (Eq. 3 falloff, Eq. 5 discretised). Outputs, for the
+ * concatenated views (P = sum of width*height):
+ *   color   [3 per view, planar]: view v occupies 3*W_v*H_v floats, channel-major
+ *   depth   [P]  sum_i w_i z_i
+ *   alpha   [P]  1 - T_final
+ *   normal  [like color]  sum_i w_i n_i
+ *   t_final [P]  final transmittance
+ *   last    [P]  one past the sorted-instance index of the last blended splat
+ *                (the tile's start if none): the backward replays [start, last)
+ *   n_contrib [P] number of blended splats
+ * normal may be NULL (not written). */
+GES_API ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                          const void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes,
+                          float *color, float *depth, float *alpha, float *normal, float *t_final,
+                          uint32_t *last, uint32_t *n_contrib, void *stream);
+
+/* S7 + S8: backward. Replays the forward front to back from t_final and last
+ * (no per-pixel lists are stored): with w_i = alpha_i T_i and X a final output,
+ * dX/dalpha_i = T_i x_i - (X - sum_{j<=i} w_j x_j) / (1 - alpha_i), and for the
+ * alpha output T_final / (1 - alpha_i). Per-splat screen-space gradients are
+ * summed across each warp before FP32 atomics into a per-entry accumulator
+ * (g2d, 16 floats per entry: u, v, conic a, b, c, opacity, beta, z, r, g, b, -,
+ * nx, ny, nz, -), which the chain rule of S1-S4 then takes back to the inputs.
+ * Inputs: the forward's inputs, `proj`/`bins` as left by ges_bin, the forward's
+ * color, depth, normal, t_final and last, and the upstream gradients (same
+ * layouts as the outputs; any of g_color, g_depth, g_alpha, g_normal may be NULL
+ * for zero). Outputs g_pos_op, g_lscale_beta, g_quat, g_color_in have the input
+ * layouts and are OVERWRITTEN (summed over views). g2d may be NULL, else it
+ * receives the per-entry screen-space gradients [n_views * n, 16]. */
+GES_API ges_status ges_render_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                          const float *pos_op, const float *lscale_beta, const float *quat, const float *color_in,
+                          void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes,
+                          const float *color, const float *depth, const float *normal, const float *t_final,
+                          const uint32_t *last, const float *g_color, const float *g_depth,
+                          const float *g_alpha, const float *g_normal, float *g_pos_op, float *g_lscale_beta,
+                          float *g_quat, float *g_color_in, float *g2d, void *stream);
+
+/* Byte offsets of the arrays inside `proj` and `bins`, for callers that inspect
+ * the intermediate results (tests, tools). Host-only; launches nothing.
+ *   proj.records  [n_views * n] x 16 float: (u, v, a, b), (c, q_cut, beta/2, o),
+ *                 (r, g, b, z), (nx, ny, nz, 0); entry e = view * n + splat
+ *   proj.binrec   [n_views * n] x 4 x 32-bit: ext_x, ext_y (float), tiles touched,
+ *                 z32 bits (uint32; 0xffffffff if culled)
+ *   proj.g2d      [n_views * n] x 16 float screen-space gradient accumulator
+ *   bins.inst_tile / inst_entry  [n_instances] uint32, sorted by (tile, z32, entry)
+ *   bins.ranges   [n_tiles] x 2 uint32 [start, end) per global tile (0, 0 if empty);
+ *                 global tile = tile_base[view] + ty * tiles_x + tx
+ *   bins.queue    [n_tiles] uint32 global tile ids, longest list first          */
+typedef struct ges_layout {
+    uint64_t proj_records, proj_binrec, proj_g2d, proj_bytes;
+    uint64_t bins_inst_tile, bins_inst_entry, bins_ranges, bins_queue, bins_bytes;
+    uint32_t n_tiles;
+    uint32_t tile_base[GES_MAX_VIEWS];
+} ges_layout;
+
+GES_API ges_status ges_get_layout(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                          uint64_t capacity, ges_layout *out);
+
+/* Synchronises `stream`, reads and clears the device error word in `proj`, and
+ * returns the first recorded condition (GES_OK if none). */
+GES_API ges_status ges_sync_status(void *proj, size_t proj_bytes, void *stream);
+
+/* Static description of a status code. */
+GES_API const char *ges_status_string(ges_status s);
+
+/* GES_ABI_VERSION of the loaded library. */
+GES_API int32_t ges_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GES_H */

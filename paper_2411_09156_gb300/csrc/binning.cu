@@ -1,0 +1,377 @@
+// S5 binning: stable LSD radix sort (reduce-then-scan, 8-bit digits), exclusive
+// scan, instance emission in depth order, tile ranges and the longest-first
+// tile queue. Instance counts are read from device memory, so the whole chain
+// runs without a host round trip and can be captured in a CUDA graph with
+// capacity-sized grids (CTAs past the live count exit at once).
+#include "ges_internal.cuh"
+
+namespace ges {
+
+// ------------------------------------------------------------------ scan
+// Exclusive scan of n uint32 in three launches: tile sums, one-CTA scan of the
+// tile sums, tile scans offset by the scanned sums. In place is allowed.
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive block scan of one value per thread (blockDim.x multiple of 32, <= 1024).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t incl = warp_incl_scan(v);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? s_warp[lane] : 0u;
+        uint32_t wi = warp_incl_scan(w);
+        if (lane < nw) s_warp[lane] = wi - w;
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    uint32_t r = incl - v + s_warp[warp];
+    total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *in, uint32_t n, uint32_t *partials) {
+    __shared__ uint32_t s_warp[33];
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    uint32_t sum = 0;
+#pragma unroll 4
+    for (int k = 0; k < kScanTile / 256; ++k) {
+        uint64_t idx = base + (uint64_t)k * 256 + threadIdx.x;
+        if (idx < n) sum += in[idx];
+    }
+    uint32_t tot;
+    block_excl_scan(sum, s_warp, tot);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// One CTA of 1024 threads scans up to kScanMaxPartials tile sums; writes the grand total.
+__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *partials, uint32_t np, uint32_t *total) {
+    __shared__ uint32_t s_warp[33];
+    constexpr int PER = kScanMaxPartials / 1024;
+    uint32_t v[PER];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        uint32_t idx = threadIdx.x * PER + k;
+        v[k] = idx < np ? partials[idx] : 0u;
+        s += v[k];
+    }
+    uint32_t tot;
+    uint32_t run = block_excl_scan(s, s_warp, tot);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        uint32_t idx = threadIdx.x * PER + k;
+        if (idx < np) partials[idx] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0 && total) *total = tot;
+}
+
+__global__ void __launch_bounds__(256) k_scan_down(const uint32_t *in, uint32_t *out, uint32_t n,
+                                                  const uint32_t *partials) {
+    __shared__ uint32_t s_data[kScanTile + kScanTile / 32];
+    __shared__ uint32_t s_warp[33];
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    constexpr int PER = kScanTile / 256;  // 16
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        uint32_t li = k * 256 + threadIdx.x;
+        uint64_t idx = base + li;
+        s_data[li + (li >> 5)] = idx < n ? in[idx] : 0u;
+    }
+    __syncthreads();
+    uint32_t v[PER];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        uint32_t li = threadIdx.x * PER + k;
+        v[k] = s_data[li + (li >> 5)];
+        s += v[k];
+    }
+    uint32_t tot;
+    uint32_t run = block_excl_scan(s, s_warp, tot) + partials[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        uint32_t li = threadIdx.x * PER + k;
+        s_data[li + (li >> 5)] = run;
+        run += v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        uint32_t li = k * 256 + threadIdx.x;
+        uint64_t idx = base + li;
+        if (idx < n) out[idx] = s_data[li + (li >> 5)];
+    }
+}
+
+cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *partials, uint32_t *total,
+                           cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint32_t nb = ceil_div_u64(n, kScanTile);
+    if (nb > (uint32_t)kScanMaxPartials) return cudaErrorInvalidValue;
+    k_scan_reduce<<<nb, 256, 0, s>>>(in, n, partials);
+    k_scan_partials<<<1, 1024, 0, s>>>(partials, nb, total);
+    k_scan_down<<<nb, 256, 0, s>>>(in, out, n, partials);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ radix sort
+// Count source: n_dev (device, clamped to cap) if given, else n_host.
+__device__ __forceinline__ uint32_t live_count(const uint32_t *n_dev, uint32_t n_host) {
+    return n_dev ? *n_dev : n_host;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *keys, const uint32_t *n_dev,
+                                                            uint32_t n_host, int shift, uint32_t nblocks,
+                                                            uint32_t *hist) {
+    __shared__ uint32_t s_h[kSortThreads / 32][256];
+    const int warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < (kSortThreads / 32) * 256; k += kSortThreads) (&s_h[0][0])[k] = 0u;
+    __syncthreads();
+    const uint32_t n = live_count(n_dev, n_host);
+    const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+    if (base < n) {
+#pragma unroll 4
+        for (int k = 0; k < kSortItems; ++k) {
+            uint64_t idx = base + (uint64_t)k * kSortThreads + threadIdx.x;
+            if (idx < n) atomicAdd(&s_h[warp][(keys[idx] >> shift) & 0xffu], 1u);
+        }
+    }
+    __syncthreads();
+    const int d = threadIdx.x;  // kSortThreads == 256 digits
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) c += s_h[w][d];
+    hist[(uint64_t)d * nblocks + blockIdx.x] = c;
+}
+
+// Stable scatter: each warp ranks a contiguous 512-key chunk in rounds of 32 with
+// match.any, keeping a per-warp running count per digit; warps are then ordered by
+// an exclusive prefix per digit and CTAs by the scanned digit-major histogram.
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *keys_in, const uint32_t *vals_in,
+                                                               uint32_t *keys_out, uint32_t *vals_out,
+                                                               const uint32_t *n_dev, uint32_t n_host, int shift,
+                                                               uint32_t nblocks, const uint32_t *hist_scanned) {
+    __shared__ uint32_t s_cnt[kSortThreads / 32][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < (kSortThreads / 32) * 256; k += kSortThreads) (&s_cnt[0][0])[k] = 0u;
+    __syncthreads();
+    const uint32_t n = live_count(n_dev, n_host);
+    const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+    if (base >= n) return;  // uniform for the CTA
+    const uint64_t wbase = base + (uint64_t)warp * (kSortItems * 32);
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
+        const bool valid = idx < n;
+        key[r] = valid ? keys_in[idx] : 0u;
+        val[r] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
+        const uint32_t d = (key[r] >> shift) & 0xffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
+        uint32_t before = 0;
+        if (valid) before = s_cnt[warp][d];
+        __syncwarp();
+        if (valid && (peers & lt_mask) == 0) s_cnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        rank[r] = valid ? before + __popc(peers & lt_mask) : 0xffffffffu;
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        uint32_t run = hist_scanned[(uint64_t)d * nblocks + blockIdx.x];
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            const uint32_t t = s_cnt[w][d];
+            s_cnt[w][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        if (rank[r] == 0xffffffffu) continue;
+        const uint32_t d = (key[r] >> shift) & 0xffu;
+        const uint32_t pos = s_cnt[warp][d] + rank[r];
+        if (keys_out) keys_out[pos] = key[r];
+        vals_out[pos] = val[r];
+    }
+}
+
+// Sorts (keys, vals) on bits [0, bits) with ceil(bits/8) passes, ping-ponging
+// between buffer 0 and 1; the result lands in buffer (passes % 2). vals[0] may be
+// NULL for "value = index". Keys are always written (tile ranges need them).
+cudaError_t radix_sort(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, const uint32_t *n_dev,
+                       uint32_t n_host_max, int bits, uint32_t *hist, uint32_t *partials, cudaStream_t s) {
+    const uint32_t nblocks = ceil_div_u64(n_host_max > 0 ? n_host_max : 1, kSortTile);
+    const int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+        const int in = p & 1, out = in ^ 1;
+        const int shift = 8 * p;
+        k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(keys[in], n_dev, n_host_max, shift, nblocks, hist);
+        cudaError_t e = exclusive_scan(hist, hist, 256u * nblocks, partials, nullptr, s);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(keys[in], (p == 0 && iota_vals) ? nullptr : vals[in],
+                                                        keys[out], vals[out], n_dev, n_host_max, shift, nblocks,
+                                                        hist);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ emission
+
+__global__ void __launch_bounds__(128) k_gather_counts(const uint32_t *sorted_e, const uint4 *binrec,
+                                                      uint32_t *counts, uint32_t n_entries) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n_entries) counts[r] = binrec[sorted_e[r]].z;
+}
+
+__global__ void __launch_bounds__(128) k_emit(EmitArgs a) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.n_entries) return;
+    const uint32_t e = a.sorted_e[r];
+    const uint4 br = a.binrec[e];
+    const uint32_t tiles = br.z;
+    if (tiles == 0) return;
+    if (*a.total >= 0xffffffffull) {  // uint32 offsets would wrap
+        if (r == 0) set_error(a.err, kErrCapacity);
+        return;
+    }
+    uint64_t off = a.offsets[r];
+    if (off + tiles > a.cap) set_error(a.err, kErrCapacity);
+    if (off >= a.cap) return;
+    const int v = (int)(e / (uint32_t)a.n);
+    const float4 r0 = a.rec[4 * (size_t)e], r1 = a.rec[4 * (size_t)e + 1];
+    const float u = r0.x, vv = r0.y, ca = r0.z, cb = r0.w, cc = r1.x;
+    const float qm = __fmul_rn(r1.y, kSupportMargin);
+    const float ext_x = __uint_as_float(br.x), ext_y = __uint_as_float(br.y);
+    const int W = a.V.width[v], H = a.V.height[v], tw = a.V.tile_w, th = a.V.tile_h;
+    const uint32_t tbase = (uint32_t)a.V.tile_base[v];
+    const int tiles_x = a.V.tiles_x[v];
+    int x0, x1, y0, y1;
+    pixel_box(u, vv, ext_x, ext_y, W, H, x0, x1, y0, y1);
+    for (int ty = y0 / th; ty <= y1 / th; ++ty) {
+        const int py0 = max(ty * th, y0), py1 = min(ty * th + th - 1, y1);
+        for (int tx = x0 / tw; tx <= x1 / tw; ++tx) {
+            const int px0 = max(tx * tw, x0), px1 = min(tx * tw + tw - 1, x1);
+            if (tile_hit(u, vv, ca, cb, cc, qm, px0, px1, py0, py1)) {
+                if (off < a.cap) {
+                    a.ikey[off] = tbase + (uint32_t)(ty * tiles_x + tx);
+                    a.ival[off] = e;
+                }
+                ++off;
+            }
+        }
+    }
+}
+
+// n_inst = min(total, cap); 0 when the total does not fit the uint32 offsets
+// (k_emit then writes nothing and records the capacity error).
+__global__ void k_set_count(const unsigned long long *total, uint64_t cap, uint32_t *n_inst) {
+    unsigned long long t = *total;
+    *n_inst = t >= 0xffffffffull ? 0u : (uint32_t)(t < cap ? t : cap);
+}
+
+__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t *keys, const uint32_t *n_dev, uint2 *ranges,
+                                                    uint32_t n_tiles) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t n = *n_dev;
+    if (i >= n) return;
+    const uint32_t k = keys[i];
+    if (k >= n_tiles) return;
+    if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
+    if (i == n - 1 || keys[i + 1] != k) ranges[k].y = i + 1;
+}
+
+// Longest-first tile queue: tiles are bucketed by list length on a log2 scale
+// (4 buckets per octave, longest first) with a one-CTA counting sort. Approximate
+// LPT order is enough for scheduling; the results do not depend on it.
+__global__ void __launch_bounds__(1024) k_lpt_queue(const uint2 *ranges, uint32_t n_tiles, uint32_t *queue) {
+    constexpr int NB = 128;
+    __shared__ uint32_t s_cnt[NB], s_off[NB];
+    if (threadIdx.x < NB) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    auto bucket = [](uint32_t len) -> int {
+        if (len == 0) return NB - 1;
+        const float l = 4.f * log2f((float)len + 1.f);
+        int b = (NB - 2) - (int)l;
+        return b < 0 ? 0 : b;
+    };
+    for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        atomicAdd(&s_cnt[bucket(r.y - r.x)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < NB; ++b) { s_off[b] = run; run += s_cnt[b]; }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        const uint32_t pos = atomicAdd(&s_off[bucket(r.y - r.x)], 1u);
+        queue[pos] = t;
+    }
+}
+
+
+__global__ void __launch_bounds__(256) k_depth_keys(const uint4 *binrec, uint32_t *keys, uint32_t n) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) keys[i] = binrec[i].w;
+}
+
+cudaError_t launch_bin(const BinArgs &a, cudaStream_t s) {
+    cudaError_t e;
+    const uint32_t nE = a.n_entries;
+    if (nE == 0) {  // no splats: every tile is empty
+        e = cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)a.V.n_tiles, s);
+        if (e != cudaSuccess) return e;
+        if (a.build_queue) k_lpt_queue<<<1, 1024, 0, s>>>(a.ranges, (uint32_t)a.V.n_tiles, a.queue);
+        return cudaGetLastError();
+    }
+    // 1. depth sort of all entries; key = z32 bits (culled: 0xffffffff), value = entry
+    k_depth_keys<<<ceil_div_u64(nE, 256), 256, 0, s>>>(a.binrec, a.dkey[0], nE);
+    uint32_t *dk[2] = {a.dkey[0], a.dkey[1]}, *dv[2] = {a.dval[0], a.dval[1]};
+    e = radix_sort(dk, dv, true, nullptr, nE, 32, a.hist, a.partials, s);
+    if (e != cudaSuccess) return e;
+    const uint32_t *sorted_e = dv[0];  // 4 passes: result back in buffer 0
+    // 2. tiles touched in depth order -> exclusive scan -> emission offsets
+    k_gather_counts<<<ceil_div_u64(nE, 128), 128, 0, s>>>(sorted_e, a.binrec, a.rcount, nE);
+    e = exclusive_scan(a.rcount, a.rcount, nE, a.partials, nullptr, s);
+    if (e != cudaSuccess) return e;
+    k_set_count<<<1, 1, 0, s>>>(a.total, a.cap, a.header);
+    // 3. emit (tile, entry) instances in depth order
+    EmitArgs ea;
+    ea.n_entries = nE; ea.n = a.n; ea.sorted_e = sorted_e; ea.offsets = a.rcount; ea.rec = a.rec;
+    ea.binrec = a.binrec; ea.total = a.total; ea.ikey = a.ikey[0]; ea.ival = a.ival[0]; ea.cap = a.cap;
+    ea.err = a.err; ea.V = a.V;
+    k_emit<<<ceil_div_u64(nE, 128), 128, 0, s>>>(ea);
+    // 4. stable sort by global tile id keeps the depth order inside each tile
+    uint32_t *ik[2] = {a.ikey[0], a.ikey[1]}, *iv[2] = {a.ival[0], a.ival[1]};
+    const uint32_t cap32 = (uint32_t)a.cap;
+    if (a.tile_bits > 0 && a.cap > 0) {
+        e = radix_sort(ik, iv, false, a.header, cap32, a.tile_bits, a.hist, a.partials, s);
+        if (e != cudaSuccess) return e;
+    }
+    const int res = ((a.tile_bits + 7) / 8) & 1;
+    // 5. tile ranges
+    e = cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)a.V.n_tiles, s);
+    if (e != cudaSuccess) return e;
+    if (a.cap > 0) k_tile_ranges<<<ceil_div_u64(a.cap, 256), 256, 0, s>>>(ik[res], a.header, a.ranges, (uint32_t)a.V.n_tiles);
+    // 6. longest-first queue for the persistent render
+    if (a.build_queue) k_lpt_queue<<<1, 1024, 0, s>>>(a.ranges, (uint32_t)a.V.n_tiles, a.queue);
+    return cudaGetLastError();
+}
+
+}  // namespace ges

@@ -1,0 +1,349 @@
+// S6 forward compositing and S7 backward replay.
+//
+// One CTA renders one tile (one thread per pixel). The tile's depth-sorted list
+// is walked in batches: each batch of splat records is gathered into shared
+// memory by the whole CTA, then every pixel evaluates the batch from shared
+// memory. A pixel stops at the transmittance cutoff; a warp leaves a batch when
+// all its lanes are done, and the CTA stops fetching batches once
+// __syncthreads_count reports no live pixel.
+//
+// The backward replays the list front to back from the stored t_final and
+// `last` (no per-pixel lists), and reduces each splat's 16 gradient values
+// across the warp with a transposing butterfly (16 shuffles for 16 values,
+// instead of 5 per value) before 16 lanes issue one coalesced set of FP32
+// atomics into the splat's 64-byte accumulator.
+#include "ges_internal.cuh"
+
+namespace ges {
+
+
+
+__device__ __forceinline__ bool next_tile(const uint32_t *queue, uint32_t *counter, uint32_t n_tiles, int it,
+                                          uint32_t *s_item, uint32_t &tile) {
+    if (queue) {
+        if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t item = *s_item;
+        __syncthreads();
+        if (item >= n_tiles) return false;
+        tile = queue[item];
+        return true;
+    }
+    if (it > 0) return false;
+    tile = blockIdx.x;
+    return true;
+}
+
+__device__ __forceinline__ int view_of_tile(const ViewSet &V, uint32_t tile) {
+    int v = 0;
+    while (v + 1 < V.n_views && (int)tile >= V.tile_base[v + 1]) ++v;
+    return v;
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
+    constexpr int NT = TW * TH;
+    extern __shared__ float4 s_rec[];  // [batch][4]
+    __shared__ uint32_t s_item;
+    const int tid = threadIdx.x;
+    const int lx = tid % TW, ly = tid / TW;
+    uint32_t tile;
+    for (int it = 0; next_tile(a.queue, a.counter, (uint32_t)a.V.n_tiles, it, &s_item, tile); ++it) {
+        const int v = view_of_tile(a.V, tile);
+        const int lt = (int)tile - a.V.tile_base[v];
+        const int tiles_x = a.V.tiles_x[v];
+        const int W = a.V.width[v], H = a.V.height[v];
+        const int px = (lt % tiles_x) * TW + lx, py = (lt / tiles_x) * TH + ly;
+        const bool inside = px < W && py < H;
+        const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+        const uint2 rg = a.ranges[tile];
+        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
+        uint32_t cnt = 0, last = rg.x;
+        bool done = !inside;
+        for (uint32_t base = rg.x; base < rg.y; base += (uint32_t)a.batch) {
+            if (__syncthreads_count(!done) == 0) break;
+            const uint32_t nb = min((uint32_t)a.batch, rg.y - base);
+            for (uint32_t k = tid; k < nb; k += NT) {
+                const float4 *r = a.rec + 4 * (size_t)a.inst_entry[base + k];
+                float4 r0 = r[0];
+                r0.w = r0.w + r0.w;  // 2b
+                s_rec[4 * k + 0] = r0;
+                s_rec[4 * k + 1] = r[1];
+                s_rec[4 * k + 2] = r[2];
+                s_rec[4 * k + 3] = r[3];
+            }
+            __syncthreads();
+            if (!done) {
+                for (uint32_t j = 0; j < nb; ++j) {
+                    const float4 r0 = s_rec[4 * j], r1 = s_rec[4 * j + 1];
+                    PairEval pe;
+                    if (!eval_pair(fpx - r0.x, fpy - r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, a.alpha_max,
+                                   a.alpha_min, pe))
+                        continue;
+                    const float Tn = __fmul_rn(T, __fsub_rn(1.f, pe.alpha));
+                    if (Tn < a.t_min) { done = true; break; }
+                    const float w = __fmul_rn(pe.alpha, T);
+                    const float4 r2 = s_rec[4 * j + 2], r3 = s_rec[4 * j + 3];
+                    C0 = __fmaf_rn(w, r2.x, C0);
+                    C1 = __fmaf_rn(w, r2.y, C1);
+                    C2 = __fmaf_rn(w, r2.z, C2);
+                    D = __fmaf_rn(w, r2.w, D);
+                    N0 = __fmaf_rn(w, r3.x, N0);
+                    N1 = __fmaf_rn(w, r3.y, N1);
+                    N2 = __fmaf_rn(w, r3.z, N2);
+                    T = Tn;
+                    ++cnt;
+                    last = base + j + 1;
+                }
+            }
+        }
+        if (inside) {
+            const long long P = (long long)W * H;
+            const long long pix = (long long)py * W + px;
+            const long long g = a.V.pix_base[v] + pix;
+            float *col = a.color + 3 * a.V.pix_base[v] + pix;
+            col[0] = __fmaf_rn(T, a.bg[0], C0);
+            col[P] = __fmaf_rn(T, a.bg[1], C1);
+            col[2 * P] = __fmaf_rn(T, a.bg[2], C2);
+            a.depth[g] = D;
+            a.alpha[g] = 1.f - T;
+            if (a.normal) {
+                float *nrm = a.normal + 3 * a.V.pix_base[v] + pix;
+                nrm[0] = N0; nrm[P] = N1; nrm[2 * P] = N2;
+            }
+            a.t_final[g] = T;
+            a.last[g] = last;
+            a.n_contrib[g] = cnt;
+        }
+    }
+}
+
+// Warp sum of 16 values by recursive halving: after the five butterfly levels
+// lane L holds the full sum of value (L >> 1) & 15 (lanes L and L^1 agree).
+__device__ __forceinline__ float warp_reduce16(float (&g)[16], int lane) {
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float send = up ? g[i] : g[i + 8];
+            const float keep = up ? g[i + 8] : g[i];
+            g[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+    }
+    {
+        const bool up = lane & 8;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float send = up ? g[i] : g[i + 4];
+            const float keep = up ? g[i + 4] : g[i];
+            g[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+    }
+    {
+        const bool up = lane & 4;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float send = up ? g[i] : g[i + 2];
+            const float keep = up ? g[i + 2] : g[i];
+            g[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+    }
+    {
+        const bool up = lane & 2;
+        const float send = up ? g[0] : g[1];
+        const float keep = up ? g[1] : g[0];
+        g[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return g[0] + __shfl_xor_sync(0xffffffffu, g[0], 1);
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
+    constexpr int NT = TW * TH;
+    extern __shared__ float4 s_rec[];  // [batch][4], then [batch] entry ids
+    uint32_t *s_ent = reinterpret_cast<uint32_t *>(s_rec + 4 * a.batch);
+    __shared__ uint32_t s_item, s_max;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int lx = tid % TW, ly = tid / TW;
+    const float ln2 = 0.69314718055994531f;
+    uint32_t tile;
+    for (int it = 0; next_tile(a.queue, a.counter, (uint32_t)a.V.n_tiles, it, &s_item, tile); ++it) {
+        const int v = view_of_tile(a.V, tile);
+        const int lt = (int)tile - a.V.tile_base[v];
+        const int tiles_x = a.V.tiles_x[v];
+        const int W = a.V.width[v], H = a.V.height[v];
+        const int px = (lt % tiles_x) * TW + lx, py = (lt / tiles_x) * TH + ly;
+        const bool inside = px < W && py < H;
+        const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+        const uint2 rg = a.ranges[tile];
+        // per-pixel forward results and upstream gradients
+        float Tend = 1.f, Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f, Df = 0.f, Nf0 = 0.f, Nf1 = 0.f, Nf2 = 0.f;
+        float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f, gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
+        uint32_t lp = rg.x;
+        if (inside) {
+            const long long P = (long long)W * H;
+            const long long pix = (long long)py * W + px;
+            const long long g = a.V.pix_base[v] + pix;
+            const long long c3 = 3 * a.V.pix_base[v] + pix;
+            Tend = a.t_final[g];
+            lp = a.last[g];
+            if (a.g_color) {
+                gC0 = a.g_color[c3]; gC1 = a.g_color[c3 + P]; gC2 = a.g_color[c3 + 2 * P];
+                Cf0 = a.color[c3]; Cf1 = a.color[c3 + P]; Cf2 = a.color[c3 + 2 * P];
+            }
+            if (a.g_depth) { gD = a.g_depth[g]; Df = a.depth[g]; }
+            if (a.g_alpha) gA = a.g_alpha[g];
+            if (a.g_normal) {
+                gN0 = a.g_normal[c3]; gN1 = a.g_normal[c3 + P]; gN2 = a.g_normal[c3 + 2 * P];
+                Nf0 = a.normal[c3]; Nf1 = a.normal[c3 + P]; Nf2 = a.normal[c3 + 2 * P];
+            }
+        }
+        if (tid == 0) s_max = rg.x;
+        __syncthreads();
+        if (lp > rg.x) atomicMax(&s_max, lp);
+        __syncthreads();
+        const uint32_t maxl = s_max;
+        float T = 1.f, Ca0 = 0.f, Ca1 = 0.f, Ca2 = 0.f, Da = 0.f, Na0 = 0.f, Na1 = 0.f, Na2 = 0.f;
+        for (uint32_t base = rg.x; base < maxl; base += (uint32_t)a.batch) {
+            __syncthreads();
+            const uint32_t nb = min((uint32_t)a.batch, maxl - base);
+            for (uint32_t k = tid; k < nb; k += NT) {
+                const uint32_t e = a.inst_entry[base + k];
+                const float4 *r = a.rec + 4 * (size_t)e;
+                float4 r0 = r[0];
+                r0.w = r0.w + r0.w;
+                s_rec[4 * k + 0] = r0;
+                s_rec[4 * k + 1] = r[1];
+                s_rec[4 * k + 2] = r[2];
+                s_rec[4 * k + 3] = r[3];
+                s_ent[k] = e;
+            }
+            __syncthreads();
+            for (uint32_t j = 0; j < nb; ++j) {
+                const uint32_t inst = base + j;
+                if (__all_sync(0xffffffffu, inst >= lp)) break;
+                float g[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) g[q] = 0.f;
+                bool contrib = false;
+                if (inst < lp) {
+                    const float4 r0 = s_rec[4 * j], r1 = s_rec[4 * j + 1];
+                    const float dx = fpx - r0.x, dy = fpy - r0.y;
+                    PairEval pe;
+                    if (eval_pair(dx, dy, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, a.alpha_max, a.alpha_min, pe)) {
+                        contrib = true;
+                        const float4 r2 = s_rec[4 * j + 2], r3 = s_rec[4 * j + 3];
+                        const float al = pe.alpha;
+                        const float w = __fmul_rn(al, T);
+                        Ca0 = __fmaf_rn(w, r2.x, Ca0);
+                        Ca1 = __fmaf_rn(w, r2.y, Ca1);
+                        Ca2 = __fmaf_rn(w, r2.z, Ca2);
+                        Da = __fmaf_rn(w, r2.w, Da);
+                        Na0 = __fmaf_rn(w, r3.x, Na0);
+                        Na1 = __fmaf_rn(w, r3.y, Na1);
+                        Na2 = __fmaf_rn(w, r3.z, Na2);
+                        const float inv = 1.f / (1.f - al);
+                        float dal = gC0 * (T * r2.x - (Cf0 - Ca0) * inv) + gC1 * (T * r2.y - (Cf1 - Ca1) * inv) +
+                                    gC2 * (T * r2.z - (Cf2 - Ca2) * inv);
+                        dal += gD * (T * r2.w - (Df - Da) * inv);
+                        dal += gN0 * (T * r3.x - (Nf0 - Na0) * inv) + gN1 * (T * r3.y - (Nf1 - Na1) * inv) +
+                               gN2 * (T * r3.z - (Nf2 - Na2) * inv);
+                        dal += gA * Tend * inv;
+                        T = __fmul_rn(T, __fsub_rn(1.f, al));
+                        const float o = r1.w, hb = r1.z;
+                        float gG = 0.f;
+                        if (pe.alpha_raw < a.alpha_max) {
+                            g[5] = dal * pe.G;
+                            gG = dal * o;
+                        }
+                        float dGdQ = 0.f, dGdb = 0.f;
+                        if (pe.Q > 0.f) {
+                            dGdQ = -0.5f * hb * __fdividef(pe.p, pe.Q) * pe.G;
+                            dGdb = -0.25f * pe.p * (lg2_approx(pe.Q) * ln2) * pe.G;
+                        }
+                        const float gQ = gG * dGdQ;
+                        const float a2 = r0.z + r0.z, b2 = r0.w, c2 = r1.x + r1.x;
+                        g[0] = -gQ * (a2 * dx + b2 * dy);
+                        g[1] = -gQ * (b2 * dx + c2 * dy);
+                        g[2] = gQ * dx * dx;
+                        g[3] = gQ * 2.f * dx * dy;
+                        g[4] = gQ * dy * dy;
+                        g[6] = gG * dGdb;
+                        g[7] = gD * w;
+                        g[8] = gC0 * w;
+                        g[9] = gC1 * w;
+                        g[10] = gC2 * w;
+                        g[12] = gN0 * w;
+                        g[13] = gN1 * w;
+                        g[14] = gN2 * w;
+                    }
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
+                    const float s = warp_reduce16(g, lane);
+                    if ((lane & 1) == 0) atomicAdd(a.g2d + 16 * (size_t)s_ent[j] + (lane >> 1), s);
+                }
+            }
+        }
+    }
+}
+
+template <int TW, int TH>
+static cudaError_t launch_fwd_t(const FwdArgs &a, int grid, cudaStream_t s) {
+    const size_t smem = (size_t)a.batch * 64;
+    k_render_fwd<TW, TH><<<grid, TW * TH, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TW, int TH>
+static cudaError_t launch_bwd_t(const BwdArgs &a, int grid, cudaStream_t s) {
+    const size_t smem = (size_t)a.batch * 68;
+    k_render_bwd<TW, TH><<<grid, TW * TH, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TW, int TH>
+static int persistent_grid(bool bwd, int batch) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (bwd)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_bwd<TW, TH>, TW * TH, (size_t)batch * 68);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_fwd<TW, TH>, TW * TH, (size_t)batch * 64);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+bool tile_shape_supported(int tw, int th) {
+    return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
+}
+
+cudaError_t launch_render_fwd(const FwdArgs &a, cudaStream_t s) {
+    const int tw = a.V.tile_w, th = a.V.tile_h;
+    int grid = a.V.n_tiles;
+    if (a.queue) {
+        grid = (tw == 16) ? persistent_grid<16, 16>(false, a.batch)
+                          : (tw == 8 ? persistent_grid<8, 8>(false, a.batch) : persistent_grid<32, 8>(false, a.batch));
+        if (grid > a.V.n_tiles) grid = a.V.n_tiles;
+    }
+    if (grid <= 0) return cudaSuccess;
+    if (tw == 16 && th == 16) return launch_fwd_t<16, 16>(a, grid, s);
+    if (tw == 8 && th == 8) return launch_fwd_t<8, 8>(a, grid, s);
+    return launch_fwd_t<32, 8>(a, grid, s);
+}
+
+cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s) {
+    const int tw = a.V.tile_w, th = a.V.tile_h;
+    int grid = a.V.n_tiles;
+    if (a.queue) {
+        grid = (tw == 16) ? persistent_grid<16, 16>(true, a.batch)
+                          : (tw == 8 ? persistent_grid<8, 8>(true, a.batch) : persistent_grid<32, 8>(true, a.batch));
+        if (grid > a.V.n_tiles) grid = a.V.n_tiles;
+    }
+    if (grid <= 0) return cudaSuccess;
+    if (tw == 16 && th == 16) return launch_bwd_t<16, 16>(a, grid, s);
+    if (tw == 8 && th == 8) return launch_bwd_t<8, 8>(a, grid, s);
+    return launch_bwd_t<32, 8>(a, grid, s);
+}
+
+}  // namespace ges

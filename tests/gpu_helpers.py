@@ -1,0 +1,123 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI,
+run the oracle on the same seeded inputs, and compare."""
+import numpy as np
+import torch
+
+from oracle import oracle as O
+from paper_2411_09156_gb300 import api
+
+# tolerances stated by the method's parity contract
+IMG_ATOL = 2e-4
+GRAD_REL_L2 = 1e-3
+
+
+def oracle_cfg(cfg: api.GESConfig, flag_eps=1e-4) -> dict:
+    return dict(phi_mode=cfg.phi_mode, rho=cfg.rho, lowpass=cfg.lowpass, alpha_min=cfg.alpha_min,
+                alpha_max=cfg.alpha_max, t_min=cfg.t_min, jac_clamp=cfg.jac_clamp, bg=tuple(cfg.bg),
+                flag_eps=flag_eps)
+
+
+def gpu_forward(scene, cams, cfg: api.GESConfig, **kw):
+    t = api.scene_tensors(scene)
+    rast = api.Rasterizer(scene.n, cams, cfg, **kw)
+    rast.forward(*t)
+    torch.cuda.synchronize()
+    return rast, t
+
+
+def view_outputs(rast, v):
+    """One view's outputs in the oracle's per-pixel layout (row-major pixels, channels last)."""
+    w, h = rast.sizes[v]
+    o = {}
+    o["color"] = rast.image("color", v).permute(1, 2, 0).reshape(-1, 3).double().cpu().numpy()
+    o["normal"] = rast.image("normal", v).permute(1, 2, 0).reshape(-1, 3).double().cpu().numpy()
+    for k in ("depth", "alpha", "t_final"):
+        o[k] = rast.image(k, v).reshape(-1).double().cpu().numpy()
+    for k in ("last", "n_contrib"):
+        o[k] = rast.image(k, v).reshape(-1).cpu().numpy().astype(np.int64)
+    return o
+
+
+def compare_forward(rast, scene, cams, cfg, v=0, pixels=None, atol=IMG_ATOL):
+    """Forward parity of one view against the oracle. Returns (report dict, oracle output, mask)."""
+    cam = cams[v].as_dict() if hasattr(cams[v], "as_dict") else cams[v]
+    ref = O.render(scene, cam, oracle_cfg(cfg), pixels=pixels)
+    got = view_outputs(rast, v)
+    w = cam["width"]
+    if pixels is not None:
+        idx = np.asarray(pixels)[:, 1] * w + np.asarray(pixels)[:, 0]
+        got = {k: a[idx] for k, a in got.items()}
+    mask = ref["flags"] == 0
+    rep = {"flagged": int((~mask).sum()), "pixels": int(mask.size)}
+    for k in ("color", "depth", "alpha", "normal"):
+        err = np.abs(got[k][mask] - ref[k][mask])
+        rep[k] = float(err.max()) if err.size else 0.0
+        assert rep[k] <= atol, (k, rep[k])
+    np.testing.assert_array_equal(got["n_contrib"][mask], ref["n_contrib"][mask])
+    # last contributor: splat id of the instance before `last`
+    n_inst = rast.capacity
+    ent = rast.bins_views(n_inst)["entry"].cpu().numpy().astype(np.int64)
+    has = got["n_contrib"] > 0
+    ids = np.full(got["last"].shape, -1, np.int64)
+    ids[has] = ent[got["last"][has] - 1] % scene.n
+    np.testing.assert_array_equal(ids[mask], ref["last_id"][mask])
+    return rep, ref, mask
+
+
+def upstream(rast, seed):
+    """Random N(0,1) upstream gradients in the rasterizer's output layouts (device tensors)."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    P = rast.P
+    gc = torch.randn(3 * P, generator=g)
+    gd = torch.randn(P, generator=g)
+    ga = torch.randn(P, generator=g)
+    gn = torch.randn(3 * P, generator=g)
+    return [x.cuda() for x in (gc, gd, ga, gn)]
+
+
+def mask_upstream(rast, grads, keep_by_view):
+    """Zero the upstream gradients outside keep_by_view[v] (bool per pixel of view v)."""
+    gc, gd, ga, gn = [x.clone() for x in grads]
+    for v, keep in enumerate(keep_by_view):
+        w, h = rast.sizes[v]
+        k = torch.as_tensor(keep, device="cuda").reshape(-1)
+        b = rast.pix_base[v]
+        gd[b:b + w * h] *= k
+        ga[b:b + w * h] *= k
+        for c in range(3):
+            gc[3 * b + c * w * h:3 * b + (c + 1) * w * h] *= k
+            gn[3 * b + c * w * h:3 * b + (c + 1) * w * h] *= k
+    return gc, gd, ga, gn
+
+
+def oracle_upstream(rast, grads, v, pixels=None):
+    """One view's upstream gradients in the oracle layout ((P,3), (P,), (P,), (P,3))."""
+    w, h = rast.sizes[v]
+    b = rast.pix_base[v]
+    gc, gd, ga, gn = [x.double().cpu().numpy() for x in grads]
+    c = gc[3 * b:3 * b + 3 * w * h].reshape(3, -1).T
+    n = gn[3 * b:3 * b + 3 * w * h].reshape(3, -1).T
+    d = gd[b:b + w * h]
+    a = ga[b:b + w * h]
+    if pixels is not None:
+        idx = np.asarray(pixels)[:, 1] * w + np.asarray(pixels)[:, 0]
+        return c[idx], d[idx], a[idx], n[idx]
+    return c, d, a, n
+
+
+def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=1e-3, floor=1e-2, rows=None):
+    """Tensor-level relative L2 and elementwise |d| <= elem * max(|g|, floor * rms(g))."""
+    rep = {}
+    for k in ("g_pos_op", "g_lscale_beta", "g_quat", "g_color"):
+        a = np.asarray(got[k], np.float64).reshape(len(got[k]), -1)
+        b = np.asarray(ref[k], np.float64).reshape(len(ref[k]), -1)
+        if rows is not None:
+            a, b = a[rows], b[rows]
+        den = np.linalg.norm(b)
+        r = float(np.linalg.norm(a - b) / max(den, 1e-30))
+        rms = float(np.sqrt(np.mean(b * b))) if b.size else 0.0
+        bad = np.abs(a - b) > elem * np.maximum(np.abs(b), floor * rms)
+        rep[k] = dict(rel_l2=r, max_abs=float(np.abs(a - b).max()) if a.size else 0.0, n_bad=int(bad.sum()))
+        assert r <= rel_l2, (k, rep[k])
+        assert bad.sum() == 0, (k, rep[k])
+    return rep

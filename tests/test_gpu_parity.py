@@ -1,0 +1,258 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: keys, order and contributor counts bit-exact; colour, depth,
+alpha and normal within 2e-4 absolute; gradients within 1e-3 relative L2 and
+elementwise 1e-3 * max(|g|, 1e-2 rms(g)). Pixels where FP32 and FP64 may
+take a threshold decision differently are flagged by the oracle, excluded from
+the image comparison (their count is asserted small) and given zero upstream
+gradient on both sides.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import binning as OB
+from oracle import oracle as O
+from paper_2411_09156_gb300 import api
+from paper_2411_09156_gb300.drt import drt_sizes
+from paper_2411_09156_gb300.scenes import look_at, make_scene, workload
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def _tiny():
+    return workload("tiny-1k-128")
+
+
+# ----------------------------------------------------------------- S1-S4
+def test_preprocess_matches_oracle():
+    sc, cams = workload("object-100k-800", n_override=20000)
+    cfg = api.GESConfig(sh_degree=3)
+    rast, _ = H.gpu_forward(sc, cams, cfg)
+    pv = rast.proj_views()
+    rec = pv["rec"].double().cpu().numpy()
+    binrec = pv["binrec"].cpu().numpy()
+    ref = O.preprocess(sc, cams[0].as_dict(), H.oracle_cfg(cfg))
+    vis_g = binrec[:, 3].astype(np.uint32) != 0xFFFFFFFF
+    vis_o = (ref["visible"] == 1)
+    # the GPU lists a splat only if it touches a tile; the oracle's visibility has no tiles
+    assert np.all(~vis_g | vis_o)
+    v = vis_g
+    np.testing.assert_array_equal(binrec[v, 3].astype(np.uint32), ref["z32"][v].view(np.uint32))
+    np.testing.assert_allclose(rec[v, 0], ref["uvz"][v, 0], rtol=1e-5, atol=2e-3)
+    np.testing.assert_allclose(rec[v, 1], ref["uvz"][v, 1], rtol=1e-5, atol=2e-3)
+    con = ref["conic"][v]
+    scale = np.abs(con).max(1, keepdims=True)
+    assert np.max(np.abs(rec[v][:, [2, 3, 4]] - con) / scale) < 2e-4
+    np.testing.assert_allclose(rec[v, 5], ref["qcut"][v], rtol=2e-5)
+    np.testing.assert_allclose(rec[v, 8:11], ref["rgb"][v], atol=2e-5)
+    np.testing.assert_allclose(rec[v, 11], ref["uvz"][v, 2], rtol=1e-6)
+    nrm_ok = v.copy()
+    np.testing.assert_allclose(rec[nrm_ok, 12:15], ref["normal"][nrm_ok], atol=2e-5)
+
+
+# ----------------------------------------------------------------- S5: bit-exact keys and order
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
+def test_binning_is_bit_exact(tile):
+    sc, _ = _tiny()
+    cams = [look_at((0.3, -3.6, 0.8), (0, 0, 0), 131, 97), look_at((-1.0, -3.0, 0.5), (0, 0, 0), 64, 80)]
+    cfg = api.GESConfig(tile_w=tile[0], tile_h=tile[1])
+    rast, _ = H.gpu_forward(sc, cams, cfg)
+    pv = rast.proj_views()
+    rec = pv["rec"].cpu().numpy()
+    binrec = pv["binrec"].cpu().numpy()
+    ext = binrec[:, :2].copy().view(np.float32)
+    vis = binrec[:, 3].astype(np.uint32) != 0xFFFFFFFF
+    recd = dict(u=rec[:, 0], v=rec[:, 1], a=rec[:, 2], b=rec[:, 3], c=rec[:, 4], qcut=rec[:, 5],
+                ext_x=ext[:, 0], ext_y=ext[:, 1])
+    z32 = binrec[:, 3].astype(np.uint32).view(np.float32)
+    views = [(c.width, c.height) for c in cams]
+    keys, ents, touched, ranges = OB.instances(recd, vis, z32, views, tile[0], tile[1], sc.n)
+    np.testing.assert_array_equal(binrec[:, 2], touched)
+    m = len(keys)
+    assert m > 1000 and rast.last_instance_count == m
+    bv = rast.bins_views(m)
+    np.testing.assert_array_equal(bv["tile"].cpu().numpy(), keys)
+    np.testing.assert_array_equal(bv["entry"].cpu().numpy(), ents)
+    np.testing.assert_array_equal(bv["ranges"].cpu().numpy(), ranges)
+    assert rast.sync_status() == 0
+
+
+# ----------------------------------------------------------------- S6
+@pytest.mark.parametrize("tile,batch", [((16, 16), 256), ((8, 8), 64), ((32, 8), 128)])
+def test_forward_tiny_scene_full_image(tile, batch):
+    sc, cams = _tiny()
+    cfg = api.GESConfig(tile_w=tile[0], tile_h=tile[1], batch=batch)
+    rast, _ = H.gpu_forward(sc, cams, cfg)
+    rep, ref, mask = H.compare_forward(rast, sc, cams, cfg)
+    assert rep["flagged"] <= 0.01 * rep["pixels"]
+    assert ref["n_contrib"].max() > 5
+
+
+def test_forward_ragged_sizes_sh3_and_background():
+    sc = make_scene(3000, 21, "object", 3)
+    cfg = api.GESConfig(sh_degree=3, bg=(0.2, 0.5, 0.8))
+    for (w, h) in ((131, 97), (17, 250), (1, 1), (300, 3)):
+        cams = [look_at((0.4, -2.5, 0.9), (0, 0, 0), w, h)]
+        rast, _ = H.gpu_forward(sc, cams, cfg)
+        rep, _, _ = H.compare_forward(rast, sc, cams, cfg)
+        assert rep["flagged"] <= max(2, 0.01 * rep["pixels"])
+
+
+def test_zero_splats_and_zero_opacity_give_background():
+    cams = [look_at((0, -4, 0), (0, 0, 0), 40, 24)]
+    cfg = api.GESConfig(bg=(0.25, 0.5, 0.75))
+    for sc in (make_scene(0, 1, "uniform", -1), make_scene(50, 1, "uniform", -1)):
+        sc.pos_op[:, 3] = 0.001
+        rast, t = H.gpu_forward(sc, cams, cfg)
+        img = rast.image("color", 0)
+        for c in range(3):
+            assert torch.all(img[c] == np.float32(cfg.bg[c]))
+        assert int(rast.out["n_contrib"].max()) == 0
+        grads = rast.backward(*t, *H.upstream(rast, 0))
+        torch.cuda.synchronize()
+        for k, g in grads.items():
+            assert torch.all(g == 0), k
+
+
+# ----------------------------------------------------------------- S7 + S8
+@pytest.mark.parametrize("sh_degree", [-1, 3])
+def test_backward_matches_oracle_gradient(sh_degree):
+    if sh_degree < 0:
+        sc, cams = _tiny()
+    else:
+        sc = make_scene(2000, 31, "object", 3)
+        cams = [look_at((0.5, -2.2, 0.7), (0, 0, 0), 96, 80)]
+    cfg = api.GESConfig(sh_degree=sh_degree, bg=(0.1, 0.2, 0.3))
+    rast, t = H.gpu_forward(sc, cams, cfg)
+    rep, ref, mask = H.compare_forward(rast, sc, cams, cfg)
+    ups = H.mask_upstream(rast, H.upstream(rast, 1000), [mask])
+    g2d = torch.empty(sc.n * 16, dtype=torch.float32, device="cuda")
+    grads = rast.backward(*t, *ups, g2d=g2d)
+    torch.cuda.synchronize()
+    got = {k: v.double().cpu().numpy() for k, v in grads.items()}
+    oc, od, oa, on = H.oracle_upstream(rast, ups, 0)
+    refg = O.backward(sc, cams[0].as_dict(), H.oracle_cfg(cfg), oc, od, oa, on)
+    H.compare_grads(got, refg)
+    # screen-space accumulators too (u, v, conic, opacity, beta, z, rgb, normal)
+    g2 = g2d.view(-1, 16).double().cpu().numpy()
+    cols = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 13, 14]
+    a, b = g2[:, cols], refg["g2d"][:, cols]
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-3
+
+
+def test_autograd_function_matches_direct_calls():
+    from paper_2411_09156_gb300.autograd import rasterize
+    sc, cams = _tiny()
+    cfg = api.GESConfig()
+    t = [x.clone().requires_grad_(True) for x in api.scene_tensors(sc)]
+    rast = api.Rasterizer(sc.n, cams, cfg)
+    c, d, a, n = rasterize(*t, rast)
+    ups = H.upstream(rast, 3)
+    loss = (c * ups[0]).sum() + (d * ups[1]).sum() + (a * ups[2]).sum() + (n * ups[3]).sum()
+    loss.backward()
+    rast2, t2 = H.gpu_forward(sc, cams, cfg)
+    direct = rast2.backward(*t2, *ups)
+    torch.cuda.synchronize()
+    for x, k in zip(t, ("g_pos_op", "g_lscale_beta", "g_quat", "g_color")):
+        r = (x.grad - direct[k]).norm() / direct[k].norm()
+        assert r < 1e-5, k
+
+
+# ----------------------------------------------------------------- forms agree bit for bit
+def test_tile_shapes_batches_and_persistent_are_bit_identical():
+    sc = make_scene(4000, 41, "object", 3)
+    cams = [look_at((0.3, -2.4, 0.6), (0, 0, 0), 150, 110)]
+    base = None
+    for cfg in (api.GESConfig(sh_degree=3), api.GESConfig(sh_degree=3, tile_w=8, tile_h=8, batch=64),
+                api.GESConfig(sh_degree=3, tile_w=32, tile_h=8, batch=96),
+                api.GESConfig(sh_degree=3, persistent=1), api.GESConfig(sh_degree=3, batch=32, persistent=1)):
+        rast, _ = H.gpu_forward(sc, cams, cfg)
+        out = {k: rast.out[k].clone() for k in ("color", "depth", "alpha", "normal", "t_final", "n_contrib")}
+        if base is None:
+            base = out
+            continue
+        for k in out:
+            assert torch.equal(out[k], base[k]), (cfg, k)
+
+
+def test_batched_views_equal_per_view_calls():
+    sc = make_scene(5000, 51, "heightfield", 2)
+    sizes = drt_sizes(160, 104, 4)
+    rng = np.random.default_rng(7)
+    cams = [look_at(5.0 * d / np.linalg.norm(d), (0, 0, 0), w, h) for d, (w, h) in zip(rng.normal(size=(4, 3)), sizes)]
+    for persistent in (0, 1):
+        cfg = api.GESConfig(sh_degree=2, persistent=persistent)
+        rast, t = H.gpu_forward(sc, cams, cfg)
+        ups = H.upstream(rast, 5)
+        gb = rast.backward(*t, *ups)
+        torch.cuda.synchronize()
+        gsum = {k: torch.zeros_like(v) for k, v in gb.items()}
+        for v, cam in enumerate(cams):
+            r1, t1 = H.gpu_forward(sc, [cam], cfg)
+            for k in ("color", "depth", "alpha", "normal", "t_final", "n_contrib"):
+                assert torch.equal(r1.image(k, 0), rast.image(k, v)), (v, k)
+            w, h = sizes[v]
+            b = rast.pix_base[v]
+            u1 = [ups[0][3 * b:3 * b + 3 * w * h], ups[1][b:b + w * h], ups[2][b:b + w * h],
+                  ups[3][3 * b:3 * b + 3 * w * h]]
+            g1 = r1.backward(*t1, *[x.contiguous() for x in u1])
+            torch.cuda.synchronize()
+            for k in gsum:
+                gsum[k] += g1[k]
+        for k in gsum:
+            r = float((gsum[k] - gb[k]).norm() / gb[k].norm())
+            assert r < 1e-5, (k, r)
+
+
+# ----------------------------------------------------------------- device-detected conditions
+def test_capacity_overflow_is_reported_and_recoverable():
+    sc, cams = _tiny()
+    cfg = api.GESConfig()
+    t = api.scene_tensors(sc)
+    rast = api.Rasterizer(sc.n, cams, cfg, capacity=100)
+    rast.forward(*t)
+    assert rast.sync_status() == 2  # GES_ERR_CAPACITY
+    assert rast.sync_status() == 0  # cleared
+    big = api.Rasterizer(sc.n, cams, cfg)
+    big.forward(*t)
+    assert big.sync_status() == 0
+
+
+# ----------------------------------------------------------------- full-size workloads, sampled
+def _sample_pixels(rng, w, h, k):
+    return np.stack([rng.integers(0, w, k), rng.integers(0, h, k)], 1).astype(np.int32)
+
+
+def test_full_size_scene_1p5m_sampled_fwd_bwd():
+    sc, cams = workload("scene-1.5M-1600x1040")
+    cfg = api.GESConfig(sh_degree=3)
+    rast, t = H.gpu_forward(sc, cams, cfg)
+    px = _sample_pixels(np.random.default_rng(0), 1600, 1040, 192)
+    rep, ref, mask = H.compare_forward(rast, sc, cams, cfg, pixels=px)
+    assert rep["flagged"] <= 4
+    keep = np.zeros(1600 * 1040, bool)
+    keep[(px[:, 1] * 1600 + px[:, 0])[mask]] = True
+    ups = H.mask_upstream(rast, H.upstream(rast, 1003), [keep])
+    grads = rast.backward(*t, *ups)
+    torch.cuda.synchronize()
+    got = {k: v.double().cpu().numpy() for k, v in grads.items()}
+    oc, od, oa, on = H.oracle_upstream(rast, ups, 0, pixels=px)
+    refg = O.backward(sc, cams[0].as_dict(), H.oracle_cfg(cfg), oc, od, oa, on, pixels=px)
+    rows = np.nonzero(np.abs(refg["g_pos_op"]).sum(1) + np.abs(got["g_pos_op"]).sum(1) > 0)[0]
+    assert len(rows) > 100
+    H.compare_grads(got, refg, rows=rows)
+
+
+def test_full_size_drt8_batch_sampled_forward():
+    sizes = drt_sizes(1600, 1040, 8)
+    sc, cams = workload("drt8-1.5M", sizes=sizes)
+    cfg = api.GESConfig(sh_degree=3, persistent=1)
+    rast, _ = H.gpu_forward(sc, cams, cfg)
+    rng = np.random.default_rng(1)
+    for v in (0, 3, 7):
+        w, h = sizes[v]
+        px = _sample_pixels(rng, w, h, 48)
+        rep, _, _ = H.compare_forward(rast, sc, cams, cfg, v=v, pixels=px)
+        assert rep["flagged"] <= 3

@@ -195,6 +195,22 @@ def test_two_splats_on_axis_hand_composite():
     assert out["n_contrib"][0] == 2 and out["last_id"][0] == 0
 
 
+def test_transmittance_cutoff_ends_the_pixel():
+    """On-axis centre pixel (Q = 0, alpha_i = o_i): after o = 0.99 and 0.985, T = 1.5e-4;
+    the next splat (o = 0.5) would take T below t_min = 1e-4, so the pixel ends there and
+    the later o = 0.1 splat, which alone would keep T above t_min, is not blended."""
+    cam = axis_camera(33, 33, 30.0)
+    ops = [0.99, 0.985, 0.5, 0.1]
+    zs = [2.0, 2.2, 2.4, 2.6]
+    sc = make_splats([[0, 0, z] for z in zs], [-2.5, -2.5, -3.0], 2.0, ops)
+    out = O.render(sc, cam, oracle_cfg(), pixels=[[16, 16]])
+    o = [float(np.float32(x)) for x in ops]
+    T = (1 - o[0]) * (1 - o[1])
+    assert out["n_contrib"][0] == 2 and out["last_id"][0] == 1
+    np.testing.assert_allclose(out["T"][0], T, rtol=1e-12)
+    np.testing.assert_allclose(out["depth"][0], o[0] * 2.0 + (1 - o[0]) * o[1] * 2.2, rtol=1e-6)
+
+
 def test_zero_opacity_gives_background_and_zero_gradient():
     sc = make_scene(40, 3, "uniform", -1)
     sc.pos_op[:, 3] = 0.5 * AMIN
