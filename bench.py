@@ -1,0 +1,441 @@
+#!/usr/bin/env python
+"""Benchmark of the GES rasterizer hot path: fwd+bwd Mpixel/s at 1.5M splats.
+
+Workload (default "drt8-1.5M"): the 1.5M-splat heightfield scene rendered into 8
+views whose sizes follow the cosine dynamic-resolution schedule of Eq. 15
+(400x260 ... 1600x1040, 6,252,862 pixels), SH degree 3, random upstream
+gradients N(0,1) on colour, depth, alpha and normal. One step is the whole hot
+path for all views: preprocess + binning, render forward, render backward,
+preprocess backward, run as captured CUDA graphs (persistent render over a
+longest-first tile queue). The same views are also timed through the plain
+one-view-per-launch path for comparison ("per_view").
+
+Prints one JSON line (rank 0). With --impl reference it times the FP64 CPU
+oracle instead (the reference arm of this benchmark), on a bounded pixel sample.
+Under torchrun each rank renders its own independent batch of views (weak
+scaling, no collective on the data path); the reported time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpixel/s at 1.5M splats, batched vs per-view, and % of HBM roofline"
+F_TEST = 10          # FP32 flops per evaluated (pixel, list entry) pair: dx, dy, Q
+F_BLEND_FWD = 26     # per blended pair in the forward (falloff, alpha, transmittance, 7 accumulations)
+F_BLEND_BWD = 104    # per blended pair in the backward replay (forward blend + 78 gradient flops)
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="drt8-1.5M")
+    p.add_argument("--no-per-view", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the oracle sample")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- workload
+def make_workload(name: str, rank: int = 0):
+    from paper_2411_09156_gb300.drt import drt_sizes
+    from paper_2411_09156_gb300.scenes import random_sphere_cameras, workload
+    if name == "drt8-1.5M":
+        sizes = drt_sizes(1600, 1040, 8)
+    elif name == "drt16-3M":
+        sizes = drt_sizes(1920, 1080, 16)
+    else:
+        sizes = None
+    sc, cams = workload(name, sizes=sizes)
+    if rank > 0 and sizes is not None:  # independent batch of views per rank
+        cams = random_sphere_cameras(np.random.default_rng(1000 + rank), len(sizes), 5.0, sizes)
+    return sc, cams
+
+
+def upstream_grads(P: int, seed: int):
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    return [torch.randn(n, generator=g, device="cuda") for n in (3 * P, P, P, 3 * P)]
+
+
+def profile_traffic(kernel: str, src_file: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_drt8-1.5M.md")
+    if not os.path.exists(path):
+        return None, None
+    txt = open(path).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    cur = hashlib.sha256(open(src_file, "rb").read()).hexdigest()
+    if not m or not b or m.group(1) != cur:
+        return None, cur
+    return float(b.group(1)), cur
+
+
+# --------------------------------------------------------------------------- CPU oracle leg
+def _oracle_cfg(cfg):
+    return dict(phi_mode=cfg.phi_mode, rho=cfg.rho, lowpass=cfg.lowpass, alpha_min=cfg.alpha_min,
+                alpha_max=cfg.alpha_max, t_min=cfg.t_min, jac_clamp=cfg.jac_clamp, bg=tuple(cfg.bg), flag_eps=1e-4)
+
+
+def run_oracle(sc, cams, cfg, n_pix: int, seed: int):
+    """Oracle forward + backward on n_pix seeded pixels spread over the views (pixel counts proportional
+    to view size). Returns elapsed seconds."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(seed)
+    sizes = [(c.width, c.height) for c in cams]
+    total = sum(w * h for w, h in sizes)
+    t0 = time.perf_counter()
+    for cam, (w, h) in zip(cams, sizes):
+        k = max(1, int(round(n_pix * w * h / total)))
+        px = np.stack([rng.integers(0, w, k), rng.integers(0, h, k)], 1).astype(np.int32)
+        d = cam.as_dict()
+        O.render(sc, d, _oracle_cfg(cfg), pixels=px)
+        g = rng.standard_normal((k, 8))
+        O.backward(sc, d, _oracle_cfg(cfg), g[:, 0:3], g[:, 3], g[:, 4], g[:, 5:8], pixels=px)
+    return time.perf_counter() - t0
+
+
+def sample_size(sc, cams, cfg, seconds: float) -> int:
+    """Pixels whose oracle fwd+bwd takes about `seconds` (fit of a fixed per-view cost plus a per-pixel cost)."""
+    t_a = run_oracle(sc, cams, cfg, 16, 11)
+    t_b = run_oracle(sc, cams, cfg, 16 + 256, 12)
+    slope = max((t_b - t_a) / 256.0, 1e-7)
+    fixed = max(t_a - 16 * slope, 0.0)
+    return int(min(max(16, (seconds - fixed) / slope), 1 << 20))
+
+
+def cpu_baseline(sc, cams, cfg, seconds: float):
+    from oracle import oracle as O
+    O.build_oracle()
+    n_final = sample_size(sc, cams, cfg, seconds)
+    t = run_oracle(sc, cams, cfg, n_final, 125)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n_final / t, n_final, t, cores
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_2411_09156_gb300.api import GESConfig
+    sc, cams = make_workload(args.workload)
+    cfg = GESConfig(sh_degree=sc.sh_degree, persistent=1)
+    from oracle import oracle as O
+    O.build_oracle()
+    # one step = a bounded sample of the workload, sized for about 6 s of host work
+    n_step = sample_size(sc, cams, cfg, 6.0)
+    for w in range(args.warmup):
+        run_oracle(sc, cams, cfg, max(16, n_step // 8), 100 + w)
+    times = [run_oracle(sc, cams, cfg, n_step, 200 + s) for s in range(args.steps)]
+    total = sum(times)
+    value = n_step * args.steps / total / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample_pixels_per_step": n_step, "views": len(cams),
+                       "splats": sc.n},
+            "cpu_baseline": {"value": value, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n_step} seeded pixels per step spread over the {len(cams)} views "
+                                       f"(fwd + analytic bwd, brute force over all {sc.n} splats)"},
+            "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    from paper_2411_09156_gb300 import api
+    from paper_2411_09156_gb300.batch import BatchPlan, autotune
+
+    torch.cuda.set_device(local)
+    dev_name = torch.cuda.get_device_name()
+    sc, cams = make_workload(args.workload, rank)
+    inputs = api.scene_tensors(sc)
+    P = sum(c.width * c.height for c in cams)
+    ups = upstream_grads(P, 1000 + rank)
+    base = api.GESConfig(sh_degree=sc.sh_degree, persistent=1)
+    cfg = base if args.no_autotune else autotune(sc.n, cams, base, inputs, ups, key=args.workload)
+    plan = BatchPlan(sc.n, cams, cfg, inputs, ups)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+
+    # warm-up (untimed), then check the device status once
+    for _ in range(args.warmup):
+        plan.step()
+    torch.cuda.synchronize()
+    plan.check()
+
+    # algorithmic work counts of the render kernels (outside the timed region)
+    n_eval = torch.empty(P, dtype=torch.int32, device="cuda")
+    plan.rast.render_fwd(n_eval=n_eval)
+    torch.cuda.synchronize()
+    o = plan.rast.out
+    evals_fwd = int(n_eval.double().sum().item())
+    blended = int(o["n_contrib"].double().sum().item())
+    lay = plan.rast.layout()
+    ranges = plan.rast.bins[lay.bins_ranges:lay.bins_ranges + 8 * lay.n_tiles].view(torch.int32).view(-1, 2)
+    starts = torch.empty(P, dtype=torch.int64, device="cuda")
+    tw, th = cfg.tile_w, cfg.tile_h
+    for v, (w, h) in enumerate(plan.rast.sizes):
+        ys, xs = torch.meshgrid(torch.arange(h, device="cuda"), torch.arange(w, device="cuda"), indexing="ij")
+        tiles = lay.tile_base[v] + (ys // th) * ((w + tw - 1) // tw) + xs // tw
+        starts[plan.rast.pix_base[v]:plan.rast.pix_base[v + 1]] = ranges[tiles.reshape(-1), 0].long()
+    evals_bwd = int((o["last"].long() - starts).double().sum().item())
+    n_inst = plan.rast.instance_count()
+    plan.step()  # restore the step's own state
+    torch.cuda.synchronize()
+
+    # timed region
+    sampler = ClockSampler(local)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between steps, outside the step's events
+        plan.step(evs[k])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier(world)
+    clocks = sampler.stop()
+    stage_ms = [[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(4)] for k in range(args.steps)]
+    step_ms = [evs[k][0].elapsed_time(evs[k][4]) for k in range(args.steps)]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    ms_per_step = total_ms / args.steps
+    value = world * P / (ms_per_step / 1e3) / 1e6
+    st = plan.rast.sync_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after the timed steps")
+    stage_avg = [statistics.mean(s[i] for s in stage_ms) for i in range(4)]
+    names = ["preprocess_bin", "render_fwd", "render_bwd", "preprocess_bwd"]
+
+    # roofline of the dominant kernel
+    dom = int(np.argmax(stage_avg))
+    sm_mhz = clocks.get("sm_mhz") or 1447.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled SM clock
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    flops_fwd = F_TEST * evals_fwd + F_BLEND_FWD * blended
+    flops_bwd = F_TEST * evals_bwd + F_BLEND_BWD * blended
+    kernels = {"render_fwd": ("k_render_fwd", flops_fwd), "render_bwd": ("k_render_bwd", flops_bwd)}
+    if names[dom] in kernels:
+        kname, fl = kernels[names[dom]]
+        achieved = fl / (stage_avg[dom] / 1e3) / 1e12
+        traffic, _ = profile_traffic(kname, os.path.join(ROOT, "paper_2411_09156_gb300", "csrc", "render.cu"))
+        roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak, "traffic": traffic,
+                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled median)",
+                    "flops_per_launch": fl}
+    else:
+        roofline = {"bound": "hbm", "kernel": names[dom], "achieved": None, "peak": hbm, "unit": "GB/s",
+                    "frac": None, "traffic": None}
+
+    # per-view path (one launch sequence per view, each captured as graphs)
+    per_view = None
+    if not args.no_per_view:
+        pv_cfg = cfg.replace(persistent=0)
+        plans = []
+        for v, cam in enumerate(cams):
+            w, h = cam.width, cam.height
+            b = plan.rast.pix_base[v]
+            u = [ups[0][3 * b:3 * b + 3 * w * h], ups[1][b:b + w * h], ups[2][b:b + w * h],
+                 ups[3][3 * b:3 * b + 3 * w * h]]
+            plans.append(BatchPlan(sc.n, [cam], pv_cfg, inputs, u))
+        for _ in range(args.warmup):
+            for p_ in plans:
+                p_.step()
+        torch.cuda.synchronize()
+        pv_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for p_ in plans:
+                p_.step()
+            e1.record()
+            torch.cuda.synchronize()
+            pv_ms.append(e0.elapsed_time(e1))
+        for p_ in plans:
+            p_.check()
+        pv = statistics.mean(pv_ms)
+        per_view = {"value": world * P / (pv / 1e3) / 1e6, "unit": "Mpixel/s", "ms_per_step": pv,
+                    "launches": f"{len(cams)} sequential one-view steps, each as CUDA graphs, one CTA per tile"}
+        del plans
+        torch.cuda.empty_cache()
+
+    # end to end through the public API with host buffers (H2D inputs + upstream, D2H gradients)
+    e2e = None
+    if not args.no_e2e:
+        host_in = [t.cpu().pin_memory() for t in inputs]
+        host_up = [t.cpu().pin_memory() for t in ups]
+        host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in plan.grads.items()}
+        h2d = sum(t.numel() * 4 for t in host_in + host_up)
+        d2h = sum(t.numel() * 4 for t in host_out.values())
+
+        def e2e_step():
+            for d, h in zip(inputs, host_in):
+                d.copy_(h, non_blocking=True)
+            for d, h in zip(ups, host_up):
+                d.copy_(h, non_blocking=True)
+            g = plan.step()
+            for k in host_out:
+                host_out[k].copy_(g[k], non_blocking=True)
+
+        for _ in range(max(1, args.warmup // 2)):
+            e2e_step()
+        torch.cuda.synchronize()
+        e_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            e2e_step()
+            e1.record()
+            torch.cuda.synchronize()
+            e_ms.append(e0.elapsed_time(e1))
+        em = max_over_ranks(statistics.mean(e_ms), world)
+        e2e = {"value": world * P / (em / 1e3) / 1e6, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": em}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, npx, secs, cores = cpu_baseline(sc, cams, cfg, args.cpu_seconds)
+        cpu = {"value": rate / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+               "sample": f"{npx} seeded pixels over the {len(cams)} views, fwd + analytic bwd, "
+                         f"brute force over all {sc.n} splats, {secs:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded heightfield scene, random upstream grads)",
+            "config": {"workload": args.workload, "splats": sc.n, "views": len(cams),
+                       "sizes": [[c.width, c.height] for c in cams], "pixels": P, "sh_degree": sc.sh_degree,
+                       "tile": [cfg.tile_w, cfg.tile_h], "batch": cfg.batch, "persistent": cfg.persistent,
+                       "instances": n_inst, "l2": "flushed between steps (256 MB write)", "gpu": dev_name,
+                       "parallelism": "replicas" if world > 1 else "single-gpu"},
+            "stages_ms": dict(zip(names, stage_avg)),
+            "roofline": roofline,
+            "per_view": per_view,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": plan.launches_per_step() * args.steps,
+            "work": {"evaluated_pairs_fwd": evals_fwd, "evaluated_pairs_bwd": evals_bwd, "blended_pairs": blended},
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -155,11 +155,13 @@ GES_API ges_status ges_bin(int32_t n, int32_t n_views, const ges_camera *cams, c
  *   last    [P]  one past the sorted-instance index of the last blended splat
  *                (the tile's start if none): the backward replays [start, last)
  *   n_contrib [P] number of blended splats
- * normal may be NULL (not written). */
+ *   n_eval  [P]  number of tile-list entries the pixel evaluated before it ended
+ *                (the work count of the pixel; used for roofline accounting)
+ * normal and n_eval may be NULL (not written). */
 GES_API ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
-                          const void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes,
-                          float *color, float *depth, float *alpha, float *normal, float *t_final,
-                          uint32_t *last, uint32_t *n_contrib, void *stream);
+                                  const void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes,
+                                  float *color, float *depth, float *alpha, float *normal, float *t_final,
+                                  uint32_t *last, uint32_t *n_contrib, uint32_t *n_eval, void *stream);
 
 /* S7 + S8: backward. Replays the forward front to back from t_final and last
  * (no per-pixel lists are stored): with w_i = alpha_i T_i and X a final output,
@@ -181,6 +183,26 @@ GES_API ges_status ges_render_bwd(int32_t n, int32_t n_views, const ges_camera *
                           const uint32_t *last, const float *g_color, const float *g_depth,
                           const float *g_alpha, const float *g_normal, float *g_pos_op, float *g_lscale_beta,
                           float *g_quat, float *g_color_in, float *g2d, void *stream);
+
+/* The two halves of ges_render_bwd, for callers that schedule or time them
+ * separately. ges_render_bwd_screen is S7 alone: it zeroes the accumulator (g2d,
+ * or the one inside `proj` if g2d is NULL) and sums every pixel's screen-space
+ * gradient into it. ges_preprocess_bwd is S8 alone: it takes that accumulator
+ * (g2d, or the one inside `proj` if NULL) back to the 3-D inputs (overwriting
+ * g_pos_op, g_lscale_beta, g_quat, g_color_in). Arguments are as for
+ * ges_render_bwd. */
+GES_API ges_status ges_render_bwd_screen(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                                         void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes,
+                                         const float *color, const float *depth, const float *normal,
+                                         const float *t_final, const uint32_t *last, const float *g_color,
+                                         const float *g_depth, const float *g_alpha, const float *g_normal,
+                                         float *g2d, void *stream);
+
+GES_API ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                                      const float *pos_op, const float *lscale_beta, const float *quat,
+                                      const float *color_in, const void *proj, size_t proj_bytes, const float *g2d,
+                                      float *g_pos_op, float *g_lscale_beta, float *g_quat, float *g_color_in,
+                                      void *stream);
 
 /* Byte offsets of the arrays inside `proj` and `bins`, for callers that inspect
  * the intermediate results (tests, tools). Host-only; launches nothing.

@@ -60,7 +60,10 @@ SIGNATURES = {
     "ges_preprocess": (ctypes.c_int, [_I, _P, _P, _P, _P, _I, _CAM, _CFG, _P, _S, _P]),
     "ges_instance_count": (ctypes.c_int, [_P, _S, ctypes.POINTER(ctypes.c_uint64), _P]),
     "ges_bin": (ctypes.c_int, [_I, _I, _CAM, _CFG, _P, _S, _P, _S, _P]),
-    "ges_render_fwd": (ctypes.c_int, [_I, _I, _CAM, _CFG, _P, _S, _P, _S, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ges_render_fwd": (ctypes.c_int, [_I, _I, _CAM, _CFG, _P, _S, _P, _S, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ges_render_bwd_screen": (ctypes.c_int, [_I, _I, _CAM, _CFG, _P, _S, _P, _S, _P, _P, _P, _P, _P, _P, _P, _P,
+                                             _P, _P, _P]),
+    "ges_preprocess_bwd": (ctypes.c_int, [_I, _I, _CAM, _CFG, _P, _P, _P, _P, _P, _S, _P, _P, _P, _P, _P, _P]),
     "ges_render_bwd": (ctypes.c_int, [_I, _I, _CAM, _CFG, _P, _P, _P, _P, _P, _S, _P, _S, _P, _P, _P, _P, _P,
                                       _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ges_sync_status": (ctypes.c_int, [_P, _S, _P]),

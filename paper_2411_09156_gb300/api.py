@@ -125,10 +125,27 @@ def ges_bin(n, n_views, cams_c, cfg_c, proj, bins, stream=None) -> None:
 
 
 def ges_render_fwd(n, n_views, cams_c, cfg_c, proj, bins, color, depth, alpha, normal, t_final, last, n_contrib,
-                   stream=None) -> None:
+                   n_eval=None, stream=None) -> None:
     check(_lib.lib().ges_render_fwd(n, n_views, cams_c, ctypes.byref(cfg_c), _ptr(proj), proj.numel(), _ptr(bins),
                                     bins.numel(), _ptr(color), _ptr(depth), _ptr(alpha), _ptr(normal),
-                                    _ptr(t_final), _ptr(last), _ptr(n_contrib), _stream(stream)), "ges_render_fwd")
+                                    _ptr(t_final), _ptr(last), _ptr(n_contrib), _ptr(n_eval), _stream(stream)),
+          "ges_render_fwd")
+
+
+def ges_render_bwd_screen(n, n_views, cams_c, cfg_c, proj, bins, color, depth, normal, t_final, last, g_color,
+                          g_depth, g_alpha, g_normal, g2d=None, stream=None) -> None:
+    check(_lib.lib().ges_render_bwd_screen(n, n_views, cams_c, ctypes.byref(cfg_c), _ptr(proj), proj.numel(),
+                                           _ptr(bins), bins.numel(), _ptr(color), _ptr(depth), _ptr(normal),
+                                           _ptr(t_final), _ptr(last), _ptr(g_color), _ptr(g_depth), _ptr(g_alpha),
+                                           _ptr(g_normal), _ptr(g2d), _stream(stream)), "ges_render_bwd_screen")
+
+
+def ges_preprocess_bwd(n, n_views, cams_c, cfg_c, pos_op, lscale_beta, quat, color_in, proj, g2d, g_pos_op,
+                       g_lscale_beta, g_quat, g_color_in, stream=None) -> None:
+    check(_lib.lib().ges_preprocess_bwd(n, n_views, cams_c, ctypes.byref(cfg_c), _ptr(pos_op), _ptr(lscale_beta),
+                                        _ptr(quat), _ptr(color_in), _ptr(proj), proj.numel(), _ptr(g2d),
+                                        _ptr(g_pos_op), _ptr(g_lscale_beta), _ptr(g_quat), _ptr(g_color_in),
+                                        _stream(stream)), "ges_preprocess_bwd")
 
 
 def ges_render_bwd(n, n_views, cams_c, cfg_c, pos_op, lscale_beta, quat, color_in, proj, bins, color, depth, normal,
@@ -223,10 +240,10 @@ class Rasterizer:
                 self._alloc_bins(max(1024, int(math.ceil(m * self.headroom))))
         ges_bin(self.n, self.n_views, self.cams_c, self.cfg_c, self.proj, self.bins, stream)
 
-    def render_fwd(self, stream=None) -> Dict[str, torch.Tensor]:
+    def render_fwd(self, stream=None, n_eval: Optional[torch.Tensor] = None) -> Dict[str, torch.Tensor]:
         o = self.out
         ges_render_fwd(self.n, self.n_views, self.cams_c, self.cfg_c, self.proj, self.bins, o["color"], o["depth"],
-                       o["alpha"], o["normal"], o["t_final"], o["last"], o["n_contrib"], stream)
+                       o["alpha"], o["normal"], o["t_final"], o["last"], o["n_contrib"], n_eval, stream)
         return o
 
     def forward(self, pos_op, lscale_beta, quat, color, stream=None) -> Dict[str, torch.Tensor]:
@@ -247,8 +264,25 @@ class Rasterizer:
                        grads["g_color"], g2d, stream)
         return grads
 
+    def backward_screen(self, g_color=None, g_depth=None, g_alpha=None, g_normal=None,
+                        g2d: Optional[torch.Tensor] = None, stream=None) -> None:
+        o = self.out
+        ges_render_bwd_screen(self.n, self.n_views, self.cams_c, self.cfg_c, self.proj, self.bins, o["color"],
+                              o["depth"], o["normal"], o["t_final"], o["last"], g_color, g_depth, g_alpha, g_normal,
+                              g2d, stream)
+
+    def preprocess_bwd(self, pos_op, lscale_beta, quat, color, grads: Dict[str, torch.Tensor],
+                       g2d: Optional[torch.Tensor] = None, stream=None) -> Dict[str, torch.Tensor]:
+        ges_preprocess_bwd(self.n, self.n_views, self.cams_c, self.cfg_c, pos_op, lscale_beta, quat, color, self.proj,
+                           g2d, grads["g_pos_op"], grads["g_lscale_beta"], grads["g_quat"], grads["g_color"], stream)
+        return grads
+
     def sync_status(self, stream=None) -> int:
         return ges_sync_status(self.proj, stream)
+
+    def instance_count(self, stream=None) -> int:
+        """Tile instances produced by the last preprocess (synchronises the stream)."""
+        return ges_instance_count(self.proj, stream)
 
     # -- views of the outputs
     def image(self, name: str, v: int) -> torch.Tensor:

@@ -1,0 +1,166 @@
+"""Batched dynamic-resolution steps as CUDA graphs, and the tile/batch autotuner.
+
+A DRT step (Eq. 15, Sec. 3.4) renders several views of uneven size forward and
+backward. BatchPlan runs it as four captured CUDA graphs -- (preprocess + bin),
+render forward, render backward (screen space), preprocess backward -- over
+buffers sized for a fixed tile-instance capacity, so a step is four graph
+launches with no host synchronisation. After a replay, `check()` reads the
+device error word; a capacity overflow re-sizes the buffers and re-captures.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+from typing import Dict, List, Optional, Sequence
+
+import torch
+
+from . import build as _build
+from .api import GESConfig, Rasterizer
+from ._lib import GES_ERR_CAPACITY, GES_OK, GESError
+
+STAGES = ("preprocess_bin", "render_fwd", "render_bwd", "preprocess_bwd")
+
+
+class BatchPlan:
+    def __init__(self, n: int, cams: Sequence, cfg: GESConfig, inputs: Sequence[torch.Tensor],
+                 upstream: Sequence[Optional[torch.Tensor]], capacity: Optional[int] = None, headroom: float = 1.15,
+                 use_graphs: bool = True):
+        self.n, self.cams, self.cfg = n, list(cams), cfg
+        self.inputs = list(inputs)
+        self.upstream = list(upstream)
+        self.headroom = headroom
+        self.use_graphs = use_graphs
+        if capacity is None:
+            probe = Rasterizer(n, cams, cfg)
+            probe.preprocess(*self.inputs)
+            capacity = max(1024, int(math.ceil(probe.instance_count() * headroom)))
+            del probe
+        self._setup(capacity)
+
+    def _setup(self, capacity: int) -> None:
+        self.rast = Rasterizer(self.n, self.cams, self.cfg, capacity=capacity)
+        self.capacity = capacity
+        self.grads = {k: torch.empty_like(t) for k, t in
+                      zip(("g_pos_op", "g_lscale_beta", "g_quat", "g_color"), self.inputs)}
+        self.graphs: List[Optional[torch.cuda.CUDAGraph]] = [None] * 4
+        if self.use_graphs:
+            self._capture()
+
+    def _run_stage(self, k: int) -> None:
+        r, x = self.rast, self.inputs
+        if k == 0:
+            r.preprocess(*x)
+            r.bin()
+        elif k == 1:
+            r.render_fwd()
+        elif k == 2:
+            r.backward_screen(*self.upstream)
+        else:
+            r.preprocess_bwd(*x, self.grads)
+
+    def _capture(self) -> None:
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for k in range(4):  # one eager pass before capture
+                self._run_stage(k)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        for k in range(4):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self._run_stage(k)
+            self.graphs[k] = g
+        torch.cuda.synchronize()
+
+    def run_stage(self, k: int) -> None:
+        if self.graphs[k] is not None:
+            self.graphs[k].replay()
+        else:
+            self._run_stage(k)
+
+    def step(self, events: Optional[List[torch.cuda.Event]] = None) -> Dict[str, torch.Tensor]:
+        """One fwd+bwd step; events (5, optional) bracket the four stages on the current stream."""
+        for k in range(4):
+            if events is not None:
+                events[k].record()
+            self.run_stage(k)
+        if events is not None:
+            events[4].record()
+        return self.grads
+
+    def check(self) -> int:
+        """Reads the device error word; on a capacity overflow grows the buffers and re-captures."""
+        st = self.rast.sync_status()
+        if st == GES_ERR_CAPACITY:
+            needed = self.rast.instance_count()
+            self._setup(max(int(needed * self.headroom), 2 * self.capacity))
+        elif st != GES_OK:
+            raise GESError(st, "batched step")
+        return st
+
+    def launches_per_step(self) -> int:
+        """Kernels of this library launched by one step (cudaMemsetAsync nodes not counted)."""
+        lay = self.rast.layout()
+        n_tiles = int(lay.n_tiles)
+        tile_bits = max(0, (n_tiles - 1).bit_length())
+        tile_passes = (tile_bits + 7) // 8
+        n_entries = self.n * len(self.cams)
+        if n_entries == 0:
+            binning = 1 if self.cfg.persistent else 0
+        else:
+            binning = 1 + 4 * 5 + 1 + 3 + 1 + 1 + tile_passes * 5 + 1 + (1 if self.cfg.persistent else 0)
+        return 1 + binning + 1 + 1 + 1
+
+
+# --------------------------------------------------------------------------- autotune
+TILE_SHAPES = ((16, 16), (8, 8), (32, 8))
+BATCHES = (128, 256)
+AUTOTUNE_FILE = os.path.join(_build.BUILD, "autotune.json")
+
+
+def autotune(n, cams, base_cfg: GESConfig, inputs, upstream, key: str, reps: int = 3,
+             persist: bool = True, candidates=None) -> GESConfig:
+    """Times one full step for each tile shape x batch size and returns the fastest config.
+    Results persist in AUTOTUNE_FILE keyed by GPU name and `key`."""
+    gpu = torch.cuda.get_device_name()
+    db = {}
+    if persist and os.path.exists(AUTOTUNE_FILE):
+        try:
+            with open(AUTOTUNE_FILE) as fh:
+                db = json.load(fh)
+        except (OSError, ValueError):
+            db = {}
+    k = f"{gpu}|{key}"
+    if k in db:
+        tw, th, b = db[k]["tile_w"], db[k]["tile_h"], db[k]["batch"]
+        return base_cfg.replace(tile_w=tw, tile_h=th, batch=b)
+    results = []
+    cand = candidates or [(tw, th, b) for (tw, th) in TILE_SHAPES for b in BATCHES]
+    for (tw, th, b) in cand:
+        cfg = base_cfg.replace(tile_w=tw, tile_h=th, batch=b)
+        plan = BatchPlan(n, cams, cfg, inputs, upstream)
+        plan.step()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(reps):
+            plan.step()
+        ev[1].record()
+        torch.cuda.synchronize()
+        results.append((ev[0].elapsed_time(ev[1]) / reps, tw, th, b))
+        del plan
+        torch.cuda.empty_cache()
+    results.sort()
+    _, tw, th, b = results[0]
+    db[k] = dict(tile_w=tw, tile_h=th, batch=b, ms=results[0][0],
+                 all=[dict(ms=r[0], tile_w=r[1], tile_h=r[2], batch=r[3]) for r in results],
+                 when=time.strftime("%Y-%m-%dT%H:%M:%S"))
+    if persist:
+        os.makedirs(os.path.dirname(AUTOTUNE_FILE), exist_ok=True)
+        with open(AUTOTUNE_FILE, "w") as fh:
+            json.dump(db, fh, indent=1)
+    return base_cfg.replace(tile_w=tw, tile_h=th, batch=b)

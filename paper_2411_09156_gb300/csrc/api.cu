@@ -247,7 +247,7 @@ ges_status ges_bin(int32_t n, int32_t n_views, const ges_camera *cams, const ges
 ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
                           const void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes, float *color,
                           float *depth, float *alpha, float *normal, float *t_final, uint32_t *last,
-                          uint32_t *n_contrib, void *stream) {
+                          uint32_t *n_contrib, uint32_t *n_eval, void *stream) {
     if (!check_views(n, n_views, cams, cfg) || !proj || !bins || !color || !depth || !alpha || !t_final || !last ||
         !n_contrib)
         return GES_ERR_INVALID_ARG;
@@ -266,7 +266,7 @@ ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *cams, co
     a.queue = cfg->persistent ? at<uint32_t>(bins, L.queue) : nullptr;
     a.counter = const_cast<uint32_t *>(at<uint32_t>(bins, 4));
     a.color = color; a.depth = depth; a.alpha = alpha; a.normal = normal; a.t_final = t_final;
-    a.last = last; a.n_contrib = n_contrib;
+    a.last = last; a.n_contrib = n_contrib; a.n_eval = n_eval;
     a.batch = cfg->batch;
     a.alpha_min = cfg->alpha_min; a.alpha_max = cfg->alpha_max; a.t_min = cfg->t_min;
     for (int c = 0; c < 3; ++c) a.bg[c] = cfg->bg[c];
@@ -275,19 +275,13 @@ ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *cams, co
     return cuda_status(launch_render_fwd(a, s));
 }
 
-ges_status ges_render_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
-                          const float *pos_op, const float *lscale_beta, const float *quat, const float *color_in,
-                          void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes, const float *color,
-                          const float *depth, const float *normal, const float *t_final, const uint32_t *last,
-                          const float *g_color, const float *g_depth, const float *g_alpha, const float *g_normal,
-                          float *g_pos_op, float *g_lscale_beta, float *g_quat, float *g_color_in, float *g2d,
-                          void *stream) {
+ges_status ges_render_bwd_screen(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                                 void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes,
+                                 const float *color, const float *depth, const float *normal, const float *t_final,
+                                 const uint32_t *last, const float *g_color, const float *g_depth,
+                                 const float *g_alpha, const float *g_normal, float *g2d, void *stream) {
     if (!check_views(n, n_views, cams, cfg) || !proj || !bins || !t_final || !last) return GES_ERR_INVALID_ARG;
     if ((g_color && !color) || (g_depth && !depth) || (g_normal && !normal)) return GES_ERR_INVALID_ARG;
-    if (n > 0 && (!pos_op || !lscale_beta || !quat || !color_in || !g_pos_op || !g_lscale_beta || !g_quat ||
-                  !g_color_in || !aligned16(pos_op) || !aligned16(lscale_beta) || !aligned16(quat) ||
-                  !aligned16(g_pos_op) || !aligned16(g_lscale_beta) || !aligned16(g_quat)))
-        return GES_ERR_INVALID_ARG;
     if (g2d && !aligned16(g2d)) return GES_ERR_INVALID_ARG;
     const ProjLayout PL = proj_layout(n, n_views);
     if (proj_bytes < PL.bytes) return GES_ERR_INVALID_ARG;
@@ -313,8 +307,22 @@ ges_status ges_render_bwd(int32_t n, int32_t n_views, const ges_camera *cams, co
     b.alpha_min = cfg->alpha_min; b.alpha_max = cfg->alpha_max;
     b.V = V;
     if (b.queue && cudaMemsetAsync(b.counter, 0, 4, s) != cudaSuccess) return GES_ERR_CUDA;
-    cudaError_t e = launch_render_bwd(b, s);
-    if (e != cudaSuccess) return GES_ERR_CUDA;
+    return cuda_status(launch_render_bwd(b, s));
+}
+
+ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                              const float *pos_op, const float *lscale_beta, const float *quat, const float *color_in,
+                              const void *proj, size_t proj_bytes, const float *g2d, float *g_pos_op,
+                              float *g_lscale_beta, float *g_quat, float *g_color_in, void *stream) {
+    if (!check_views(n, n_views, cams, cfg) || !proj) return GES_ERR_INVALID_ARG;
+    if (n > 0 && (!pos_op || !lscale_beta || !quat || !color_in || !g_pos_op || !g_lscale_beta || !g_quat ||
+                  !g_color_in || !aligned16(pos_op) || !aligned16(lscale_beta) || !aligned16(quat) ||
+                  !aligned16(g_pos_op) || !aligned16(g_lscale_beta) || !aligned16(g_quat)))
+        return GES_ERR_INVALID_ARG;
+    if (g2d && !aligned16(g2d)) return GES_ERR_INVALID_ARG;
+    const ProjLayout PL = proj_layout(n, n_views);
+    if (proj_bytes < PL.bytes) return GES_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     PreBwdArgs p;
     p.n = n;
     p.pos_op = reinterpret_cast<const float4 *>(pos_op);
@@ -322,14 +330,33 @@ ges_status ges_render_bwd(int32_t n, int32_t n_views, const ges_camera *cams, co
     p.quat = reinterpret_cast<const float4 *>(quat);
     p.color = color_in;
     p.rec = at<float4>(proj, PL.records);
-    p.g2d = reinterpret_cast<const float4 *>(acc);
+    p.g2d = reinterpret_cast<const float4 *>(g2d ? g2d : at<float>(proj, PL.g2d));
     p.g_pos_op = reinterpret_cast<float4 *>(g_pos_op);
     p.g_lsb = reinterpret_cast<float4 *>(g_lscale_beta);
     p.g_quat = reinterpret_cast<float4 *>(g_quat);
     p.g_color = g_color_in;
     p.P = make_params(cfg);
-    p.V = V;
+    p.V = make_views(n_views, cams, cfg);
     return cuda_status(launch_preprocess_bwd(p, s));
+}
+
+ges_status ges_render_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                          const float *pos_op, const float *lscale_beta, const float *quat, const float *color_in,
+                          void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes, const float *color,
+                          const float *depth, const float *normal, const float *t_final, const uint32_t *last,
+                          const float *g_color, const float *g_depth, const float *g_alpha, const float *g_normal,
+                          float *g_pos_op, float *g_lscale_beta, float *g_quat, float *g_color_in, float *g2d,
+                          void *stream) {
+    // check both halves' arguments before launching either
+    if (n > 0 && (!pos_op || !lscale_beta || !quat || !color_in || !g_pos_op || !g_lscale_beta || !g_quat ||
+                  !g_color_in || !aligned16(pos_op) || !aligned16(lscale_beta) || !aligned16(quat) ||
+                  !aligned16(g_pos_op) || !aligned16(g_lscale_beta) || !aligned16(g_quat)))
+        return GES_ERR_INVALID_ARG;
+    ges_status st = ges_render_bwd_screen(n, n_views, cams, cfg, proj, proj_bytes, bins, bins_bytes, color, depth,
+                                          normal, t_final, last, g_color, g_depth, g_alpha, g_normal, g2d, stream);
+    if (st != GES_OK) return st;
+    return ges_preprocess_bwd(n, n_views, cams, cfg, pos_op, lscale_beta, quat, color_in, proj, proj_bytes, g2d,
+                              g_pos_op, g_lscale_beta, g_quat, g_color_in, stream);
 }
 
 ges_status ges_sync_status(void *proj, size_t proj_bytes, void *stream) {

@@ -352,7 +352,7 @@ struct FwdArgs {
     const uint32_t *queue;  // NULL: one CTA per tile
     uint32_t *counter;
     float *color, *depth, *alpha, *normal, *t_final;
-    uint32_t *last, *n_contrib;
+    uint32_t *last, *n_contrib, *n_eval;
     int batch;
     float alpha_min, alpha_max, t_min;
     float bg[3];

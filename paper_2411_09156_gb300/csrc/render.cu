@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
         const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
         const uint2 rg = a.ranges[tile];
         float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
-        uint32_t cnt = 0, last = rg.x;
+        uint32_t cnt = 0, last = rg.x, stop = rg.y;
         bool done = !inside;
         for (uint32_t base = rg.x; base < rg.y; base += (uint32_t)a.batch) {
             if (__syncthreads_count(!done) == 0) break;
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
                                    a.alpha_min, pe))
                         continue;
                     const float Tn = __fmul_rn(T, __fsub_rn(1.f, pe.alpha));
-                    if (Tn < a.t_min) { done = true; break; }
+                    if (Tn < a.t_min) { done = true; stop = base + j + 1; break; }
                     const float w = __fmul_rn(pe.alpha, T);
                     const float4 r2 = s_rec[4 * j + 2], r3 = s_rec[4 * j + 3];
                     C0 = __fmaf_rn(w, r2.x, C0);
@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
             a.t_final[g] = T;
             a.last[g] = last;
             a.n_contrib[g] = cnt;
+            if (a.n_eval) a.n_eval[g] = stop - rg.x;
         }
     }
 }
