@@ -54,7 +54,8 @@
  *    near-plane cull (z32 > znear).
  *  - Tile lists: tile t lists a splat iff the minimum of Q over the rectangle of
  *    pixel centres of t (clipped to the splat's pixel box) is <= q_cut (1 + 2^-10),
- *    evaluated in float32 without fused multiply-adds in a fixed operation order.
+ *    evaluated in float32 without fused multiply-adds in a fixed operation order
+ *    (edge minimisers use the correctly rounded reciprocals of the conic's a, c).
  */
 #ifndef GES_H
 #define GES_H
@@ -109,7 +110,7 @@ typedef struct ges_config {
 } ges_config;
 
 /* Number of bytes `proj` must hold for n splats and n_views views:
- * per (view, splat) a 64-byte render record, a 16-byte binning record and a
+ * per (view, splat) a 64-byte render record, a 32-byte binning record and a
  * 64-byte screen-space gradient accumulator, plus a 256-byte header. */
 GES_API size_t ges_proj_bytes(int32_t n, int32_t n_views);
 
@@ -208,8 +209,10 @@ GES_API ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_came
  * the intermediate results (tests, tools). Host-only; launches nothing.
  *   proj.records  [n_views * n] x 16 float: (u, v, a, b), (c, q_cut, beta/2, o),
  *                 (r, g, b, z), (nx, ny, nz, 0); entry e = view * n + splat
- *   proj.binrec   [n_views * n] x 4 x 32-bit: ext_x, ext_y (float), tiles touched,
- *                 z32 bits (uint32; 0xffffffff if culled)
+ *   proj.binrec   [n_views * n] x 8 x 32-bit: ext_x, ext_y (float), tiles touched,
+ *                 z32 bits (uint32; 0xffffffff if not listed), hit mask over the
+ *                 tile box (row-major; valid when the box has <= 32 tiles), box
+ *                 origin tx0 | ty0 << 16, box size w | h << 16, 0
  *   proj.g2d      [n_views * n] x 16 float screen-space gradient accumulator
  *   bins.inst_tile / inst_entry  [n_instances] uint32, sorted by (tile, z32, entry)
  *   bins.ranges   [n_tiles] x 2 uint32 [start, end) per global tile (0, 0 if empty);

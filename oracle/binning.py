@@ -40,19 +40,21 @@ def rect_min_q(a, b, c, X0, X1, Y0, Y1):
     """Minimum of Q(X, Y) = a X^2 + 2 b X Y + c Y^2 over [X0, X1] x [Y0, Y1] (float32 steps).
 
     Q is convex; if the rectangle holds the origin the minimum is 0, otherwise it
-    lies on an edge, where it is the clamped 1-D minimiser of a quadratic.
+    lies on an edge, where it is the clamped 1-D minimiser of a quadratic, found
+    with the float32 reciprocals 1/a and 1/c.
     """
     a, b, c, X0, X1, Y0, Y1 = map(F, (a, b, c, X0, X1, Y0, Y1))
     if X0 <= 0 <= X1 and Y0 <= 0 <= Y1:
         return F(0.0)
     b2 = F(b + b)
+    ia, ic = F(F(1.0) / a), F(F(1.0) / c)  # correctly rounded reciprocals
     best = F(np.inf)
     for X in (X0, X1):
-        ys = F(F(-F(b * X)) / c)
+        ys = F(F(-F(b * X)) * ic)
         ys = min(max(ys, Y0), Y1)
         best = min(best, _qf(a, b2, c, X, ys))
     for Y in (Y0, Y1):
-        xs = F(F(-F(b * Y)) / a)
+        xs = F(F(-F(b * Y)) * ia)
         xs = min(max(xs, X0), X1)
         best = min(best, _qf(a, b2, c, xs, Y))
     return best

@@ -298,7 +298,7 @@ class Rasterizer:
         lay = self.layout()
         nv = self.n * self.n_views
         rec = self.proj[lay.proj_records:lay.proj_records + nv * 64].view(torch.float32).view(nv, 16)
-        binrec = self.proj[lay.proj_binrec:lay.proj_binrec + nv * 16].view(torch.int32).view(nv, 4)
+        binrec = self.proj[lay.proj_binrec:lay.proj_binrec + nv * 32].view(torch.int32).view(nv, 8)
         g2d = self.proj[lay.proj_g2d:lay.proj_g2d + nv * 64].view(torch.float32).view(nv, 16)
         return dict(rec=rec, binrec=binrec, g2d=g2d)
 

@@ -234,14 +234,14 @@ cudaError_t radix_sort(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, con
 __global__ void __launch_bounds__(128) k_gather_counts(const uint32_t *sorted_e, const uint4 *binrec,
                                                       uint32_t *counts, uint32_t n_entries) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n_entries) counts[r] = binrec[sorted_e[r]].z;
+    if (r < n_entries) counts[r] = binrec[2 * (size_t)sorted_e[r]].z;
 }
 
 __global__ void __launch_bounds__(128) k_emit(EmitArgs a) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.n_entries) return;
     const uint32_t e = a.sorted_e[r];
-    const uint4 br = a.binrec[e];
+    const uint4 br = a.binrec[2 * (size_t)e];
     const uint32_t tiles = br.z;
     if (tiles == 0) return;
     if (*a.total >= 0xffffffffull) {  // uint32 offsets would wrap
@@ -251,21 +251,38 @@ __global__ void __launch_bounds__(128) k_emit(EmitArgs a) {
     uint64_t off = a.offsets[r];
     if (off + tiles > a.cap) set_error(a.err, kErrCapacity);
     if (off >= a.cap) return;
+    const uint4 bx = a.binrec[2 * (size_t)e + 1];
     const int v = (int)(e / (uint32_t)a.n);
+    const uint32_t tbase = (uint32_t)a.V.tile_base[v];
+    const int tiles_x = a.V.tiles_x[v];
+    const int tx0 = (int)(bx.y & 0xffffu), ty0 = (int)(bx.y >> 16);
+    const int rw = (int)(bx.z & 0xffffu), rh = (int)(bx.z >> 16);
+    if (rw * rh <= 32) {  // the preprocess kept the hits as a row-major bit mask over the tile box
+        uint32_t m = bx.x;
+        while (m) {
+            const int bit = __ffs(m) - 1;
+            m &= m - 1;
+            if (off < a.cap) {
+                a.ikey[off] = tbase + (uint32_t)((ty0 + bit / rw) * tiles_x + tx0 + bit % rw);
+                a.ival[off] = e;
+            }
+            ++off;
+        }
+        return;
+    }
     const float4 r0 = a.rec[4 * (size_t)e], r1 = a.rec[4 * (size_t)e + 1];
     const float u = r0.x, vv = r0.y, ca = r0.z, cb = r0.w, cc = r1.x;
     const float qm = __fmul_rn(r1.y, kSupportMargin);
+    const float ia = __frcp_rn(ca), ic = __frcp_rn(cc);
     const float ext_x = __uint_as_float(br.x), ext_y = __uint_as_float(br.y);
     const int W = a.V.width[v], H = a.V.height[v], tw = a.V.tile_w, th = a.V.tile_h;
-    const uint32_t tbase = (uint32_t)a.V.tile_base[v];
-    const int tiles_x = a.V.tiles_x[v];
     int x0, x1, y0, y1;
     pixel_box(u, vv, ext_x, ext_y, W, H, x0, x1, y0, y1);
     for (int ty = y0 / th; ty <= y1 / th; ++ty) {
         const int py0 = max(ty * th, y0), py1 = min(ty * th + th - 1, y1);
         for (int tx = x0 / tw; tx <= x1 / tw; ++tx) {
             const int px0 = max(tx * tw, x0), px1 = min(tx * tw + tw - 1, x1);
-            if (tile_hit(u, vv, ca, cb, cc, qm, px0, px1, py0, py1)) {
+            if (tile_hit(u, vv, ca, cb, cc, ia, ic, qm, px0, px1, py0, py1)) {
                 if (off < a.cap) {
                     a.ikey[off] = tbase + (uint32_t)(ty * tiles_x + tx);
                     a.ival[off] = e;
@@ -328,7 +345,7 @@ __global__ void __launch_bounds__(1024) k_lpt_queue(const uint2 *ranges, uint32_
 
 __global__ void __launch_bounds__(256) k_depth_keys(const uint4 *binrec, uint32_t *keys, uint32_t n) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) keys[i] = binrec[i].w;
+    if (i < n) keys[i] = binrec[2 * (size_t)i].w;
 }
 
 cudaError_t launch_bin(const BinArgs &a, cudaStream_t s) {

@@ -45,7 +45,7 @@ struct Params {
 };
 
 // ------------------------------------------------------------------ layouts
-// proj: [header 256 B][records nV x 64 B][binrec nV x 16 B][g2d nV x 64 B]
+// proj: [header 256 B][records nV x 64 B][binrec nV x 32 B][g2d nV x 64 B]
 // header: u64 instance total at 0, u32 error word at 8.
 struct ProjLayout {
     uint64_t records, binrec, g2d, bytes;
@@ -58,7 +58,7 @@ inline ProjLayout proj_layout(int32_t n, int32_t n_views) {
     ProjLayout L;
     L.records = 256;
     L.binrec = align256(L.records + nv * 64);
-    L.g2d = align256(L.binrec + nv * 16);
+    L.g2d = align256(L.binrec + nv * 32);
     L.bytes = align256(L.g2d + nv * 64);
     return L;
 }
@@ -143,8 +143,9 @@ __device__ __forceinline__ float quad_rn(float a, float b2, float c, float X, fl
 // Minimum of Q over the rectangle of pixel centres [px0..px1] x [py0..py1],
 // compared with qm. Q is convex: 0 if the rectangle holds the centre, else the
 // minimum lies on an edge at the clamped 1-D minimiser.
-__device__ __forceinline__ bool tile_hit(float u, float v, float a, float b, float c, float qm, int px0, int px1,
-                                         int py0, int py1) {
+// ia, ic are the correctly rounded reciprocals 1/a, 1/c.
+__device__ __forceinline__ bool tile_hit(float u, float v, float a, float b, float c, float ia, float ic, float qm,
+                                         int px0, int px1, int py0, int py1) {
     const float X0 = __fsub_rn(__fadd_rn((float)px0, 0.5f), u);
     const float X1 = __fsub_rn(__fadd_rn((float)px1, 0.5f), u);
     const float Y0 = __fsub_rn(__fadd_rn((float)py0, 0.5f), v);
@@ -153,18 +154,18 @@ __device__ __forceinline__ bool tile_hit(float u, float v, float a, float b, flo
     const float b2 = __fadd_rn(b, b);
     float best = __int_as_float(0x7f800000);
     {
-        float ys = __fdiv_rn(-__fmul_rn(b, X0), c);
+        float ys = __fmul_rn(-__fmul_rn(b, X0), ic);
         ys = fminf(fmaxf(ys, Y0), Y1);
         best = fminf(best, quad_rn(a, b2, c, X0, ys));
-        ys = __fdiv_rn(-__fmul_rn(b, X1), c);
+        ys = __fmul_rn(-__fmul_rn(b, X1), ic);
         ys = fminf(fmaxf(ys, Y0), Y1);
         best = fminf(best, quad_rn(a, b2, c, X1, ys));
     }
     {
-        float xs = __fdiv_rn(-__fmul_rn(b, Y0), a);
+        float xs = __fmul_rn(-__fmul_rn(b, Y0), ia);
         xs = fminf(fmaxf(xs, X0), X1);
         best = fminf(best, quad_rn(a, b2, c, xs, Y0));
-        xs = __fdiv_rn(-__fmul_rn(b, Y1), a);
+        xs = __fmul_rn(-__fmul_rn(b, Y1), ia);
         xs = fminf(fmaxf(xs, X0), X1);
         best = fminf(best, quad_rn(a, b2, c, xs, Y1));
     }
@@ -293,7 +294,7 @@ struct PreArgs {
     const float4 *pos_op, *lsb, *quat;
     const float *color;
     float4 *rec;     // [nV][4]
-    uint4 *binrec;   // [nV]
+    uint4 *binrec;   // [nV][2]
     unsigned long long *total;
     uint32_t *err;
     Params P;

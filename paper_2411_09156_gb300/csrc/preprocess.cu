@@ -14,155 +14,176 @@ namespace ges {
 // S3: q_cut = (2 ln(o / alpha_min))^(2/beta), the alpha_min level set of
 //     exp(-1/2 Q^(beta/2))                                          (Eq. 3)
 // S4: colour from SH, normal = R[:, argmin l] facing the camera   (Sec. 3.3)
+//
+// Sigma' is accumulated as sum_k s'_k^2 u_k u_k^T + h I with u_k = J W r_k the
+// image of the splat's k-th axis: the same matrix as J W Sigma W^T J^T, without
+// forming the 3x3 Sigma, whose tiny contribution along the flat axis of a
+// flattened splat would be lost to float32 rounding.
+//
+// One thread per (splat, view), views innermost: the threads of one splat are
+// adjacent, so its attributes are fetched from memory once per warp and the
+// records of four splats x eight views are written as eight contiguous runs.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_preprocess(PreArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long my_tiles = 0;
-    if (i < a.n) {
-        const float4 po = a.pos_op[i];
-        const float4 ls = a.lsb[i];
-        const float4 q4 = a.quat[i];
-        const float o = po.w, beta = ls.w;
-        const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
-        const float qinv = rsqrtf(qn2);
-        float R[9];
-        quat_rot(q4.x * qinv, q4.y * qinv, q4.z * qinv, q4.w * qinv, R);
-        float dphi;
-        const float phi = phi_beta(beta, a.P.rho, a.P.phi_mode, dphi);
-        const float s0 = phi * expf(ls.x), s1 = phi * expf(ls.y), s2 = phi * expf(ls.z);
-        const float d0 = s0 * s0, d1 = s1 * s1, d2 = s2 * s2;
-        // symmetric Sigma
-        const float S00 = R[0] * R[0] * d0 + R[1] * R[1] * d1 + R[2] * R[2] * d2;
-        const float S01 = R[0] * R[3] * d0 + R[1] * R[4] * d1 + R[2] * R[5] * d2;
-        const float S02 = R[0] * R[6] * d0 + R[1] * R[7] * d1 + R[2] * R[8] * d2;
-        const float S11 = R[3] * R[3] * d0 + R[4] * R[4] * d1 + R[5] * R[5] * d2;
-        const float S12 = R[3] * R[6] * d0 + R[4] * R[7] * d1 + R[5] * R[8] * d2;
-        const float S22 = R[6] * R[6] * d0 + R[7] * R[7] * d1 + R[8] * R[8] * d2;
-        const bool op_ok = o >= a.P.alpha_min;
-        const float qcut = op_ok ? powf(2.f * logf(o / a.P.alpha_min), 2.f / beta) : 0.f;
-        const float qm = __fmul_rn(qcut, kSupportMargin);
-        int ks = 0;
-        if (ls.y < ls.x) ks = 1;
-        if (ls.z < (ks == 0 ? ls.x : ls.y)) ks = 2;
-        const float nx = R[0 + ks], ny = R[3 + ks], nz = R[6 + ks];
-        // colour coefficients held in registers across views
-        float sh[16][3];
-        const int K = a.P.n_coeffs;
-        if (a.P.sh_degree >= 0) {
-            const float *c = a.color + (size_t)i * K * 3;
+__device__ __forceinline__ void load_sh_rgb(const float *color, int K, size_t i, const float *Y, float &r, float &g,
+                                            float &b) {
+    r = 0.5f; g = 0.5f; b = 0.5f;
+    if (K == 16) {
+        const float4 *c4 = reinterpret_cast<const float4 *>(color + i * 48);
+        float c[48];
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if (k < K) { sh[k][0] = c[3 * k]; sh[k][1] = c[3 * k + 1]; sh[k][2] = c[3 * k + 2]; }
-        } else {
-            sh[0][0] = a.color[3 * i]; sh[0][1] = a.color[3 * i + 1]; sh[0][2] = a.color[3 * i + 2];
+        for (int q = 0; q < 12; ++q) {
+            const float4 x = __ldg(c4 + q);
+            c[4 * q] = x.x; c[4 * q + 1] = x.y; c[4 * q + 2] = x.z; c[4 * q + 3] = x.w;
         }
-        const bool finite_in = isfinite(po.x) && isfinite(po.y) && isfinite(po.z) && isfinite(S00) &&
-                               isfinite(S11) && isfinite(S22) && isfinite(qcut) && isfinite(beta) && beta > 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            r = fmaf(c[3 * k], Y[k], r);
+            g = fmaf(c[3 * k + 1], Y[k], g);
+            b = fmaf(c[3 * k + 2], Y[k], b);
+        }
+    } else {
+        const float *c = color + i * (size_t)K * 3;
+        for (int k = 0; k < K; ++k) {
+            r = fmaf(__ldg(c + 3 * k), Y[k], r);
+            g = fmaf(__ldg(c + 3 * k + 1), Y[k], g);
+            b = fmaf(__ldg(c + 3 * k + 2), Y[k], b);
+        }
+    }
+    r = fmaxf(r, 0.f); g = fmaxf(g, 0.f); b = fmaxf(b, 0.f);
+}
 
-        for (int v = 0; v < a.V.n_views; ++v) {
-            const size_t e = (size_t)v * a.n + i;
-            const float *vm = a.V.vm[v];
-            const float z32 = depth32(vm, po.x, po.y, po.z);
-            uint32_t tiles = 0;
-            float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
-            float ext_x = 0.f, ext_y = 0.f;
-            bool visible = op_ok && finite_in && z32 > a.V.znear[v];
-            if (visible) {
-                const float tx = vm[0] * po.x + vm[1] * po.y + vm[2] * po.z + vm[3];
-                const float ty = vm[4] * po.x + vm[5] * po.y + vm[6] * po.z + vm[7];
-                const float tz = z32;
-                const float fx = a.V.fx[v], fy = a.V.fy[v];
-                const float iz = 1.f / tz;
-                const float rx = fminf(fmaxf(tx * iz, -a.V.limx[v]), a.V.limx[v]);
-                const float ry = fminf(fmaxf(ty * iz, -a.V.limy[v]), a.V.limy[v]);
-                const float J00 = fx * iz, J02 = -fx * rx * iz, J11 = fy * iz, J12 = -fy * ry * iz;
-                // T = J W (2x3)
-                const float T00 = J00 * vm[0] + J02 * vm[8], T01 = J00 * vm[1] + J02 * vm[9], T02 = J00 * vm[2] + J02 * vm[10];
-                const float T10 = J11 * vm[4] + J12 * vm[8], T11 = J11 * vm[5] + J12 * vm[9], T12 = J11 * vm[6] + J12 * vm[10];
-                // U = T Sigma
-                const float U00 = T00 * S00 + T01 * S01 + T02 * S02;
-                const float U01 = T00 * S01 + T01 * S11 + T02 * S12;
-                const float U02 = T00 * S02 + T01 * S12 + T02 * S22;
-                const float U10 = T10 * S00 + T11 * S01 + T12 * S02;
-                const float U11 = T10 * S01 + T11 * S11 + T12 * S12;
-                const float U12 = T10 * S02 + T11 * S12 + T12 * S22;
-                const float A = U00 * T00 + U01 * T01 + U02 * T02 + a.P.lowpass;
-                const float B = U00 * T10 + U01 * T11 + U02 * T12;
-                const float C = U10 * T10 + U11 * T11 + U12 * T12 + a.P.lowpass;
-                const float det = A * C - B * B;
-                const float idet = 1.f / det;
-                const float ca = C * idet, cb = -B * idet, cc = A * idet;
-                const float u = fx * tx * iz + a.V.cx[v];
-                const float vv = fy * ty * iz + a.V.cy[v];
-                if (!(det > 0.f) || !isfinite(ca) || !isfinite(cb) || !isfinite(cc) || !isfinite(u) ||
-                    !isfinite(vv)) {
-                    visible = false;
-                    set_error(a.err, kErrNumeric);
-                } else {
-                    ext_x = sqrtf(__fmul_rn(A, qm));
-                    ext_y = sqrtf(__fmul_rn(C, qm));
-                    // tile overlap (S3): pixel box, then the exact ellipse-rectangle test per tile
-                    const int W = a.V.width[v], H = a.V.height[v], tw = a.V.tile_w, th = a.V.tile_h;
-                    int x0, x1, y0, y1;
-                    pixel_box(u, vv, ext_x, ext_y, W, H, x0, x1, y0, y1);
-                    if (x0 <= x1 && y0 <= y1) {
-                        for (int ty_ = y0 / th; ty_ <= y1 / th; ++ty_) {
-                            const int py0 = max(ty_ * th, y0), py1 = min(ty_ * th + th - 1, y1);
-                            for (int tx_ = x0 / tw; tx_ <= x1 / tw; ++tx_) {
-                                const int px0 = max(tx_ * tw, x0), px1 = min(tx_ * tw + tw - 1, x1);
-                                tiles += tile_hit(u, vv, ca, cb, cc, qm, px0, px1, py0, py1) ? 1u : 0u;
+__global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
+    const int NV = a.V.n_views;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long my_tiles = 0;
+    if (t < (long long)a.n * NV) {
+        const int i = (int)(t / NV), v = (int)(t - (long long)i * NV);
+        const size_t e = (size_t)v * a.n + i;
+        const float4 po = __ldg(a.pos_op + i);
+        const float4 ls = __ldg(a.lsb + i);
+        const float4 q4 = __ldg(a.quat + i);
+        const float o = po.w, beta = ls.w;
+        const float *vm = a.V.vm[v];
+        const float z32 = depth32(vm, po.x, po.y, po.z);
+        uint32_t tiles = 0, mask = 0, rect = 0, rdim = 0;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+        float ext_x = 0.f, ext_y = 0.f;
+        const bool op_ok = o >= a.P.alpha_min;
+        bool visible = op_ok && isfinite(po.x) && isfinite(po.y) && isfinite(po.z) && isfinite(beta) && beta > 0.f &&
+                       z32 > a.V.znear[v];
+        if (visible) {
+            const float qinv = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+            float R[9];
+            quat_rot(q4.x * qinv, q4.y * qinv, q4.z * qinv, q4.w * qinv, R);
+            float dphi;
+            const float phi = phi_beta(beta, a.P.rho, a.P.phi_mode, dphi);
+            const float sx = phi * expf(ls.x), sy = phi * expf(ls.y), sz = phi * expf(ls.z);
+            const float dk[3] = {sx * sx, sy * sy, sz * sz};
+            const float qcut = powf(2.f * logf(o / a.P.alpha_min), 2.f / beta);
+            const float qm = __fmul_rn(qcut, kSupportMargin);
+            const float tx = vm[0] * po.x + vm[1] * po.y + vm[2] * po.z + vm[3];
+            const float ty = vm[4] * po.x + vm[5] * po.y + vm[6] * po.z + vm[7];
+            const float tz = z32;
+            const float fx = a.V.fx[v], fy = a.V.fy[v];
+            const float iz = 1.f / tz;
+            const float rx = fminf(fmaxf(tx * iz, -a.V.limx[v]), a.V.limx[v]);
+            const float ry = fminf(fmaxf(ty * iz, -a.V.limy[v]), a.V.limy[v]);
+            const float J00 = fx * iz, J02 = -fx * rx * iz, J11 = fy * iz, J12 = -fy * ry * iz;
+            const float T00 = J00 * vm[0] + J02 * vm[8], T01 = J00 * vm[1] + J02 * vm[9], T02 = J00 * vm[2] + J02 * vm[10];
+            const float T10 = J11 * vm[4] + J12 * vm[8], T11 = J11 * vm[5] + J12 * vm[9], T12 = J11 * vm[6] + J12 * vm[10];
+            float A = a.P.lowpass, B = 0.f, C = a.P.lowpass;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float ux = T00 * R[k] + T01 * R[3 + k] + T02 * R[6 + k];
+                const float uy = T10 * R[k] + T11 * R[3 + k] + T12 * R[6 + k];
+                A = fmaf(dk[k] * ux, ux, A);
+                B = fmaf(dk[k] * ux, uy, B);
+                C = fmaf(dk[k] * uy, uy, C);
+            }
+            const float det = A * C - B * B;
+            const float idet = 1.f / det;
+            const float ca = C * idet, cb = -B * idet, cc = A * idet;
+            const float u = fx * tx * iz + a.V.cx[v];
+            const float vv = fy * ty * iz + a.V.cy[v];
+            if (!(det > 0.f) || !isfinite(ca) || !isfinite(cb) || !isfinite(cc) || !isfinite(u) || !isfinite(vv) ||
+                !isfinite(qcut)) {
+                visible = false;
+                set_error(a.err, kErrNumeric);
+            } else {
+                ext_x = sqrtf(__fmul_rn(A, qm));
+                ext_y = sqrtf(__fmul_rn(C, qm));
+                // tile overlap (S3): pixel box, then the ellipse-rectangle test per tile;
+                // for boxes of at most 32 tiles the hits are kept as a bit mask for emission
+                const int W = a.V.width[v], H = a.V.height[v], tw = a.V.tile_w, th = a.V.tile_h;
+                int x0, x1, y0, y1;
+                pixel_box(u, vv, ext_x, ext_y, W, H, x0, x1, y0, y1);
+                if (x0 <= x1 && y0 <= y1) {
+                    const int tx0 = x0 / tw, tx1 = x1 / tw, ty0 = y0 / th, ty1 = y1 / th;
+                    const int rw = tx1 - tx0 + 1, rh = ty1 - ty0 + 1;
+                    const float ia = __frcp_rn(ca), ic = __frcp_rn(cc);
+                    int bit = 0;
+                    for (int ty_ = ty0; ty_ <= ty1; ++ty_) {
+                        const int py0 = max(ty_ * th, y0), py1 = min(ty_ * th + th - 1, y1);
+                        for (int tx_ = tx0; tx_ <= tx1; ++tx_, ++bit) {
+                            const int px0 = max(tx_ * tw, x0), px1 = min(tx_ * tw + tw - 1, x1);
+                            if (tile_hit(u, vv, ca, cb, cc, ia, ic, qm, px0, px1, py0, py1)) {
+                                ++tiles;
+                                if (bit < 32) mask |= 1u << bit;
                             }
                         }
                     }
-                    // colour
-                    float rgb0, rgb1, rgb2;
-                    if (a.P.sh_degree >= 0) {
-                        float dx = po.x - a.V.campos[v][0], dy = po.y - a.V.campos[v][1], dz = po.z - a.V.campos[v][2];
-                        const float dinv = rsqrtf(dx * dx + dy * dy + dz * dz);
-                        dx *= dinv; dy *= dinv; dz *= dinv;
-                        float Y[16];
-                        sh_eval(a.P.sh_degree, dx, dy, dz, Y);
-                        rgb0 = 0.5f; rgb1 = 0.5f; rgb2 = 0.5f;
-#pragma unroll
-                        for (int k = 0; k < 16; ++k)
-                            if (k < K) {
-                                rgb0 = fmaf(sh[k][0], Y[k], rgb0);
-                                rgb1 = fmaf(sh[k][1], Y[k], rgb1);
-                                rgb2 = fmaf(sh[k][2], Y[k], rgb2);
-                            }
-                        rgb0 = fmaxf(rgb0, 0.f); rgb1 = fmaxf(rgb1, 0.f); rgb2 = fmaxf(rgb2, 0.f);
-                    } else {
-                        rgb0 = sh[0][0]; rgb1 = sh[0][1]; rgb2 = sh[0][2];
-                    }
-                    // normal faces the camera: sign of n . (campos - mu)
-                    const float f = nx * (a.V.campos[v][0] - po.x) + ny * (a.V.campos[v][1] - po.y) +
-                                    nz * (a.V.campos[v][2] - po.z);
-                    const float sg = f < 0.f ? -1.f : 1.f;
-                    r0 = make_float4(u, vv, ca, cb);
-                    r1 = make_float4(cc, qcut, 0.5f * beta, o);
-                    r2 = make_float4(rgb0, rgb1, rgb2, tz);
-                    r3 = make_float4(sg * nx, sg * ny, sg * nz, 0.f);
+                    rect = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
+                    rdim = (uint32_t)rw | ((uint32_t)rh << 16);
                 }
+                // colour
+                float rgb0, rgb1, rgb2;
+                if (a.P.sh_degree >= 0) {
+                    float dx = po.x - a.V.campos[v][0], dy = po.y - a.V.campos[v][1], dz = po.z - a.V.campos[v][2];
+                    const float dinv = rsqrtf(dx * dx + dy * dy + dz * dz);
+                    dx *= dinv; dy *= dinv; dz *= dinv;
+                    float Y[16];
+                    sh_eval(a.P.sh_degree, dx, dy, dz, Y);
+                    load_sh_rgb(a.color, a.P.n_coeffs, (size_t)i, Y, rgb0, rgb1, rgb2);
+                } else {
+                    rgb0 = __ldg(a.color + 3 * (size_t)i);
+                    rgb1 = __ldg(a.color + 3 * (size_t)i + 1);
+                    rgb2 = __ldg(a.color + 3 * (size_t)i + 2);
+                }
+                // normal: axis of the smallest scale, facing the camera
+                int ks = 0;
+                if (ls.y < ls.x) ks = 1;
+                if (ls.z < (ks == 0 ? ls.x : ls.y)) ks = 2;
+                const float nx = R[0 + ks], ny = R[3 + ks], nz = R[6 + ks];
+                const float f = nx * (a.V.campos[v][0] - po.x) + ny * (a.V.campos[v][1] - po.y) +
+                                nz * (a.V.campos[v][2] - po.z);
+                const float sg = f < 0.f ? -1.f : 1.f;
+                r0 = make_float4(u, vv, ca, cb);
+                r1 = make_float4(cc, qcut, 0.5f * beta, o);
+                r2 = make_float4(rgb0, rgb1, rgb2, tz);
+                r3 = make_float4(sg * nx, sg * ny, sg * nz, 0.f);
             }
-            a.rec[4 * e + 0] = r0;
-            a.rec[4 * e + 1] = r1;
-            a.rec[4 * e + 2] = r2;
-            a.rec[4 * e + 3] = r3;
-            const uint32_t key = (visible && tiles > 0) ? __float_as_uint(z32) : kCulledKey;
-            a.binrec[e] = make_uint4(__float_as_uint(ext_x), __float_as_uint(ext_y), visible ? tiles : 0u, key);
-            my_tiles += visible ? tiles : 0u;
         }
+        a.rec[4 * e + 0] = r0;
+        a.rec[4 * e + 1] = r1;
+        a.rec[4 * e + 2] = r2;
+        a.rec[4 * e + 3] = r3;
+        const bool listed = visible && tiles > 0;
+        const uint32_t key = listed ? __float_as_uint(z32) : kCulledKey;
+        a.binrec[2 * e] = make_uint4(__float_as_uint(ext_x), __float_as_uint(ext_y), listed ? tiles : 0u, key);
+        a.binrec[2 * e + 1] = make_uint4(mask, rect, rdim, 0u);
+        my_tiles += listed ? tiles : 0u;
     }
     // block reduction of the tile count, one atomic per CTA
-    __shared__ unsigned long long s_sum[4];
-    unsigned long long t = my_tiles;
+    __shared__ unsigned long long s_sum[8];
+    unsigned long long tsum = my_tiles;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = t;
+    for (int off = 16; off > 0; off >>= 1) tsum += __shfl_down_sync(0xffffffffu, tsum, off);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = tsum;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long s = s_sum[0] + s_sum[1] + s_sum[2] + s_sum[3];
-        if (s) atomicAdd(a.total, s);
+        unsigned long long sum = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += s_sum[w];
+        if (sum) atomicAdd(a.total, sum);
     }
 }
 
@@ -190,31 +211,17 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
     const float sp[3] = {phi * e0, phi * e1, phi * e2};
     const float es[3] = {e0, e1, e2};
     const float dd[3] = {sp[0] * sp[0], sp[1] * sp[1], sp[2] * sp[2]};
-    float Sig[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            Sig[r * 3 + c] = R[r * 3 + 0] * R[c * 3 + 0] * dd[0] + R[r * 3 + 1] * R[c * 3 + 1] * dd[1] +
-                             R[r * 3 + 2] * R[c * 3 + 2] * dd[2];
     int ks = 0;
     if (ls.y < ls.x) ks = 1;
     if (ls.z < (ks == 0 ? ls.x : ls.y)) ks = 2;
     const int K = a.P.n_coeffs;
-    float sh[16][3];
-    if (a.P.sh_degree >= 0) {
-        const float *c = a.color + (size_t)i * K * 3;
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < K) { sh[k][0] = c[3 * k]; sh[k][1] = c[3 * k + 1]; sh[k][2] = c[3 * k + 2]; }
-    }
-    // accumulators
+    // accumulators over views
     float gmu[3] = {0.f, 0.f, 0.f}, gop = 0.f, gl[3] = {0.f, 0.f, 0.f}, gbeta = 0.f;
     float GR[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float gD[3] = {0.f, 0.f, 0.f};  // dL/d(s'_k^2)
     float gsh[16][3];
 #pragma unroll
     for (int k = 0; k < 16; ++k) { gsh[k][0] = 0.f; gsh[k][1] = 0.f; gsh[k][2] = 0.f; }
-    float GS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma summed over views: 00 01 02 11 12 22
 
     for (int v = 0; v < a.V.n_views; ++v) {
         const size_t e = (size_t)v * a.n + i;
@@ -245,25 +252,24 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
         const float t10 = gB * ca + gC * cb, t11 = gB * cb + gC * cc;
         const float M00 = -(ca * t00 + cb * t10), M01 = -(ca * t01 + cb * t11);
         const float M11 = -(cb * t01 + cc * t11);
-        // Sigma' = T Sigma T^T: G_Sigma += T^T G_M T ; G_T = 2 G_M T Sigma
-        float GT[6];
+        // Sigma' = sum_k s'_k^2 u_k u_k^T + h I with u_k = T r_k. With w_k = G_M u_k:
+        //   dL/d(s'_k^2) += u_k . w_k,  dL/dR[:, k] += 2 s'_k^2 T^T w_k,
+        //   dL/dT = 2 sum_k s'_k^2 w_k r_k^T
+        // (equal to G_Sigma = T^T G_M T, G_R = 2 G_Sigma R D, G_T = 2 G_M T Sigma, but
+        // without the cancellation of forming G_Sigma for a nearly flat splat)
+        float GT[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float ts0 = T[0] * Sig[0 * 3 + c] + T[1] * Sig[1 * 3 + c] + T[2] * Sig[2 * 3 + c];
-            const float ts1 = T[3] * Sig[0 * 3 + c] + T[4] * Sig[1 * 3 + c] + T[5] * Sig[2 * 3 + c];
-            GT[c] = 2.f * (M00 * ts0 + M01 * ts1);
-            GT[3 + c] = 2.f * (M01 * ts0 + M11 * ts1);
-        }
-        {
-            // GS[r][c] += sum_ab T[a][r] M[a][b] T[b][c]
-            const float m0[3] = {M00 * T[0] + M01 * T[3], M00 * T[1] + M01 * T[4], M00 * T[2] + M01 * T[5]};
-            const float m1[3] = {M01 * T[0] + M11 * T[3], M01 * T[1] + M11 * T[4], M01 * T[2] + M11 * T[5]};
-            GS[0] += T[0] * m0[0] + T[3] * m1[0];
-            GS[1] += T[0] * m0[1] + T[3] * m1[1];
-            GS[2] += T[0] * m0[2] + T[3] * m1[2];
-            GS[3] += T[1] * m0[1] + T[4] * m1[1];
-            GS[4] += T[1] * m0[2] + T[4] * m1[2];
-            GS[5] += T[2] * m0[2] + T[5] * m1[2];
+        for (int k = 0; k < 3; ++k) {
+            const float ux = T[0] * R[k] + T[1] * R[3 + k] + T[2] * R[6 + k];
+            const float uy = T[3] * R[k] + T[4] * R[3 + k] + T[5] * R[6 + k];
+            const float wx = M00 * ux + M01 * uy, wy = M01 * ux + M11 * uy;
+            gD[k] += ux * wx + uy * wy;
+            const float s2 = 2.f * dd[k];
+            GR[0 + k] += s2 * (T[0] * wx + T[3] * wy);
+            GR[3 + k] += s2 * (T[1] * wx + T[4] * wy);
+            GR[6 + k] += s2 * (T[2] * wx + T[5] * wy);
+            GT[0] += s2 * wx * R[k]; GT[1] += s2 * wx * R[3 + k]; GT[2] += s2 * wx * R[6 + k];
+            GT[3] += s2 * wy * R[k]; GT[4] += s2 * wy * R[3 + k]; GT[5] += s2 * wy * R[6 + k];
         }
         // T = J W: G_J = G_T W^T (only the non-zero entries of J matter)
         const float GJ00 = GT[0] * vm[0] + GT[1] * vm[1] + GT[2] * vm[2];
@@ -301,6 +307,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
             float Y[16], dY[16][3];
             sh_eval(a.P.sh_degree, dx, dy, dz, Y);
             sh_grad(a.P.sh_degree, dx, dy, dz, dY);
+            const float *cf = a.color + (size_t)i * K * 3;
             const float gc[3] = {g2.x, g2.y, g2.z};
             float gd0 = 0.f, gd1 = 0.f, gd2 = 0.f;
 #pragma unroll
@@ -308,13 +315,13 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
                 float pre = 0.5f;
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    if (k < K) pre = fmaf(sh[k][ch], Y[k], pre);
+                    if (k < K) pre = fmaf(__ldg(cf + 3 * k + ch), Y[k], pre);
                 if (!(pre > 0.f)) continue;
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
                     if (k < K) {
                         gsh[k][ch] += gc[ch] * Y[k];
-                        const float w = gc[ch] * sh[k][ch];
+                        const float w = gc[ch] * __ldg(cf + 3 * k + ch);
                         gd0 += w * dY[k][0]; gd1 += w * dY[k][1]; gd2 += w * dY[k][2];
                     }
             }
@@ -326,23 +333,10 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
             gsh[0][0] += g2.x; gsh[0][1] += g2.y; gsh[0][2] += g2.z;
         }
     }
-    // Sigma = R D R^T: G_R += 2 G_S R D ; g_D = diag(R^T G_S R)
-    const float GSm[9] = {GS[0], GS[1], GS[2], GS[1], GS[3], GS[4], GS[2], GS[4], GS[5]};
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float acc = GSm[r * 3 + 0] * R[0 * 3 + k] + GSm[r * 3 + 1] * R[1 * 3 + k] + GSm[r * 3 + 2] * R[2 * 3 + k];
-            GR[r * 3 + k] += 2.f * acc * dd[k];
-        }
+    // s'_k = phi(beta) exp(l_k): dL/dl_k = 2 s'_k^2 gD_k, dL/dbeta += 2 s'_k gD_k phi'(beta) exp(l_k)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float gD = 0.f;
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) gD += R[r * 3 + k] * GSm[r * 3 + c] * R[c * 3 + k];
-        const float gsp = 2.f * sp[k] * gD;
+        const float gsp = 2.f * sp[k] * gD[k];
         gl[k] = gsp * sp[k];
         gbeta += gsp * dphi * es[k];
     }
@@ -368,7 +362,8 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
 
 cudaError_t launch_preprocess(const PreArgs &a, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    k_preprocess<<<(a.n + 127) / 128, 128, 0, s>>>(a);
+    const long long threads = (long long)a.n * a.V.n_views;
+    k_preprocess<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

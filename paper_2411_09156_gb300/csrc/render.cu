@@ -40,22 +40,85 @@ __device__ __forceinline__ int view_of_tile(const ViewSet &V, uint32_t tile) {
     return v;
 }
 
+// Warp footprint inside a tile: 8 x 4 pixels, so that a warp's pixels are
+// compact and a splat can be culled for the whole warp at once.
+constexpr int kWarpW = 8, kWarpH = 4;
+
+template <int TW>
+__device__ __forceinline__ void warp_pixel(int tid, int &lx, int &ly, int &wx0, int &wy0) {
+    constexpr int WPR = TW / kWarpW;
+    const int warp = tid >> 5, lane = tid & 31;
+    wx0 = (warp % WPR) * kWarpW;
+    wy0 = (warp / WPR) * kWarpH;
+    lx = wx0 + (lane & 7);
+    ly = wy0 + (lane >> 3);
+}
+
+// Culling fields of a staged batch, structure-of-arrays so that 32 lanes testing
+// 32 splats read consecutive words: u, v, a, b, c, q_cut (1 + 2^-10), 1/a, 1/c.
+constexpr int kCullFields = 8;
+
+__device__ __forceinline__ void stage_record(const float4 *rec, uint32_t e, uint32_t k, int batch, float4 *s_rec,
+                                             float *s_cull) {
+    const float4 *r = rec + 4 * (size_t)e;
+    float4 r0 = r[0];
+    const float4 r1 = r[1];
+    s_cull[0 * batch + k] = r0.x;
+    s_cull[1 * batch + k] = r0.y;
+    s_cull[2 * batch + k] = r0.z;
+    s_cull[3 * batch + k] = r0.w;
+    s_cull[4 * batch + k] = r1.x;
+    s_cull[5 * batch + k] = r1.y * kSupportMargin;
+    s_cull[6 * batch + k] = 1.f / r0.z;
+    s_cull[7 * batch + k] = 1.f / r1.x;
+    r0.w = r0.w + r0.w;  // 2b for the pair evaluation
+    s_rec[4 * k + 0] = r0;
+    s_rec[4 * k + 1] = r1;
+    s_rec[4 * k + 2] = r[2];
+    s_rec[4 * k + 3] = r[3];
+}
+
+// Can the support Q <= q_cut of staged splat j reach the rectangle of pixel
+// centres [rx0, rx1] x [ry0, ry1]? Minimum of the convex Q over the rectangle:
+// 0 if it holds the centre, else on an edge at the clamped 1-D minimiser.
+// Conservative: the margin on q_cut absorbs the rounding of this estimate.
+__device__ __forceinline__ bool warp_may_hit(const float *s_cull, int batch, uint32_t j, float rx0, float rx1,
+                                             float ry0, float ry1) {
+    const float u = s_cull[j], v = s_cull[batch + j];
+    const float a = s_cull[2 * batch + j], b = s_cull[3 * batch + j], c = s_cull[4 * batch + j];
+    const float qm = s_cull[5 * batch + j], ia = s_cull[6 * batch + j], ic = s_cull[7 * batch + j];
+    const float X0 = rx0 - u, X1 = rx1 - u, Y0 = ry0 - v, Y1 = ry1 - v;
+    if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
+    const float b2 = b + b;
+    auto q = [&](float X, float Y) { return fmaf(a * X, X, fmaf(b2 * X, Y, c * Y * Y)); };
+    float best = q(X0, fminf(fmaxf(-b * X0 * ic, Y0), Y1));
+    best = fminf(best, q(X1, fminf(fmaxf(-b * X1 * ic, Y0), Y1)));
+    best = fminf(best, q(fminf(fmaxf(-b * Y0 * ia, X0), X1), Y0));
+    best = fminf(best, q(fminf(fmaxf(-b * Y1 * ia, X0), X1), Y1));
+    return best <= qm;
+}
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
     constexpr int NT = TW * TH;
-    extern __shared__ float4 s_rec[];  // [batch][4]
+    extern __shared__ float4 s_rec[];  // [batch][4], then the culling fields [8][batch]
+    float *s_cull = reinterpret_cast<float *>(s_rec + 4 * a.batch);
     __shared__ uint32_t s_item;
-    const int tid = threadIdx.x;
-    const int lx = tid % TW, ly = tid / TW;
+    const int tid = threadIdx.x, lane = tid & 31;
+    int lx, ly, wx0, wy0;
+    warp_pixel<TW>(tid, lx, ly, wx0, wy0);
     uint32_t tile;
     for (int it = 0; next_tile(a.queue, a.counter, (uint32_t)a.V.n_tiles, it, &s_item, tile); ++it) {
         const int v = view_of_tile(a.V, tile);
         const int lt = (int)tile - a.V.tile_base[v];
         const int tiles_x = a.V.tiles_x[v];
         const int W = a.V.width[v], H = a.V.height[v];
-        const int px = (lt % tiles_x) * TW + lx, py = (lt / tiles_x) * TH + ly;
+        const int tx0 = (lt % tiles_x) * TW, ty0 = (lt / tiles_x) * TH;
+        const int px = tx0 + lx, py = ty0 + ly;
         const bool inside = px < W && py < H;
         const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+        const float rx0 = (float)(tx0 + wx0) + 0.5f, rx1 = rx0 + (float)(kWarpW - 1);
+        const float ry0 = (float)(ty0 + wy0) + 0.5f, ry1 = ry0 + (float)(kWarpH - 1);
         const uint2 rg = a.ranges[tile];
         float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
         uint32_t cnt = 0, last = rg.x, stop = rg.y;
@@ -63,25 +126,24 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
         for (uint32_t base = rg.x; base < rg.y; base += (uint32_t)a.batch) {
             if (__syncthreads_count(!done) == 0) break;
             const uint32_t nb = min((uint32_t)a.batch, rg.y - base);
-            for (uint32_t k = tid; k < nb; k += NT) {
-                const float4 *r = a.rec + 4 * (size_t)a.inst_entry[base + k];
-                float4 r0 = r[0];
-                r0.w = r0.w + r0.w;  // 2b
-                s_rec[4 * k + 0] = r0;
-                s_rec[4 * k + 1] = r[1];
-                s_rec[4 * k + 2] = r[2];
-                s_rec[4 * k + 3] = r[3];
-            }
+            for (uint32_t k = tid; k < nb; k += NT) stage_record(a.rec, a.inst_entry[base + k], k, a.batch, s_rec, s_cull);
             __syncthreads();
-            if (!done) {
-                for (uint32_t j = 0; j < nb; ++j) {
+            if (__all_sync(0xffffffffu, done)) continue;
+            for (uint32_t c0 = 0; c0 < nb; c0 += 32) {
+                const uint32_t jl = c0 + lane;
+                const bool hit = jl < nb && warp_may_hit(s_cull, a.batch, jl, rx0, rx1, ry0, ry1);
+                uint32_t mask = __ballot_sync(0xffffffffu, hit);
+                while (mask) {
+                    const uint32_t j = c0 + (uint32_t)(__ffs(mask) - 1);
+                    mask &= mask - 1;
+                    if (done) continue;
                     const float4 r0 = s_rec[4 * j], r1 = s_rec[4 * j + 1];
                     PairEval pe;
                     if (!eval_pair(fpx - r0.x, fpy - r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, a.alpha_max,
                                    a.alpha_min, pe))
                         continue;
                     const float Tn = __fmul_rn(T, __fsub_rn(1.f, pe.alpha));
-                    if (Tn < a.t_min) { done = true; stop = base + j + 1; break; }
+                    if (Tn < a.t_min) { done = true; stop = base + j + 1; continue; }
                     const float w = __fmul_rn(pe.alpha, T);
                     const float4 r2 = s_rec[4 * j + 2], r3 = s_rec[4 * j + 3];
                     C0 = __fmaf_rn(w, r2.x, C0);
@@ -95,6 +157,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
                     ++cnt;
                     last = base + j + 1;
                 }
+                if (__all_sync(0xffffffffu, done)) break;
             }
         }
         if (inside) {
@@ -161,11 +224,13 @@ __device__ __forceinline__ float warp_reduce16(float (&g)[16], int lane) {
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
     constexpr int NT = TW * TH;
-    extern __shared__ float4 s_rec[];  // [batch][4], then [batch] entry ids
-    uint32_t *s_ent = reinterpret_cast<uint32_t *>(s_rec + 4 * a.batch);
+    extern __shared__ float4 s_rec[];  // [batch][4], culling fields [8][batch], entry ids [batch]
+    float *s_cull = reinterpret_cast<float *>(s_rec + 4 * a.batch);
+    uint32_t *s_ent = reinterpret_cast<uint32_t *>(s_cull + kCullFields * a.batch);
     __shared__ uint32_t s_item, s_max;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int lx = tid % TW, ly = tid / TW;
+    int lx, ly, wx0, wy0;
+    warp_pixel<TW>(tid, lx, ly, wx0, wy0);
     const float ln2 = 0.69314718055994531f;
     uint32_t tile;
     for (int it = 0; next_tile(a.queue, a.counter, (uint32_t)a.V.n_tiles, it, &s_item, tile); ++it) {
@@ -173,9 +238,12 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
         const int lt = (int)tile - a.V.tile_base[v];
         const int tiles_x = a.V.tiles_x[v];
         const int W = a.V.width[v], H = a.V.height[v];
-        const int px = (lt % tiles_x) * TW + lx, py = (lt / tiles_x) * TH + ly;
+        const int tx0 = (lt % tiles_x) * TW, ty0 = (lt / tiles_x) * TH;
+        const int px = tx0 + lx, py = ty0 + ly;
         const bool inside = px < W && py < H;
         const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+        const float rx0 = (float)(tx0 + wx0) + 0.5f, rx1 = rx0 + (float)(kWarpW - 1);
+        const float ry0 = (float)(ty0 + wy0) + 0.5f, ry1 = ry0 + (float)(kWarpH - 1);
         const uint2 rg = a.ranges[tile];
         // per-pixel forward results and upstream gradients
         float Tend = 1.f, Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f, Df = 0.f, Nf0 = 0.f, Nf1 = 0.f, Nf2 = 0.f;
@@ -210,94 +278,97 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
             const uint32_t nb = min((uint32_t)a.batch, maxl - base);
             for (uint32_t k = tid; k < nb; k += NT) {
                 const uint32_t e = a.inst_entry[base + k];
-                const float4 *r = a.rec + 4 * (size_t)e;
-                float4 r0 = r[0];
-                r0.w = r0.w + r0.w;
-                s_rec[4 * k + 0] = r0;
-                s_rec[4 * k + 1] = r[1];
-                s_rec[4 * k + 2] = r[2];
-                s_rec[4 * k + 3] = r[3];
+                stage_record(a.rec, e, k, a.batch, s_rec, s_cull);
                 s_ent[k] = e;
             }
             __syncthreads();
-            for (uint32_t j = 0; j < nb; ++j) {
-                const uint32_t inst = base + j;
-                if (__all_sync(0xffffffffu, inst >= lp)) break;
-                float g[16];
+            for (uint32_t c0 = 0; c0 < nb; c0 += 32) {
+                if (__all_sync(0xffffffffu, base + c0 >= lp)) break;
+                const uint32_t jl = c0 + lane;
+                const bool hit = jl < nb && warp_may_hit(s_cull, a.batch, jl, rx0, rx1, ry0, ry1);
+                uint32_t mask = __ballot_sync(0xffffffffu, hit);
+                while (mask) {
+                    const uint32_t j = c0 + (uint32_t)(__ffs(mask) - 1);
+                    mask &= mask - 1;
+                    float g[16];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) g[q] = 0.f;
-                bool contrib = false;
-                if (inst < lp) {
-                    const float4 r0 = s_rec[4 * j], r1 = s_rec[4 * j + 1];
-                    const float dx = fpx - r0.x, dy = fpy - r0.y;
-                    PairEval pe;
-                    if (eval_pair(dx, dy, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, a.alpha_max, a.alpha_min, pe)) {
-                        contrib = true;
-                        const float4 r2 = s_rec[4 * j + 2], r3 = s_rec[4 * j + 3];
-                        const float al = pe.alpha;
-                        const float w = __fmul_rn(al, T);
-                        Ca0 = __fmaf_rn(w, r2.x, Ca0);
-                        Ca1 = __fmaf_rn(w, r2.y, Ca1);
-                        Ca2 = __fmaf_rn(w, r2.z, Ca2);
-                        Da = __fmaf_rn(w, r2.w, Da);
-                        Na0 = __fmaf_rn(w, r3.x, Na0);
-                        Na1 = __fmaf_rn(w, r3.y, Na1);
-                        Na2 = __fmaf_rn(w, r3.z, Na2);
-                        const float inv = 1.f / (1.f - al);
-                        float dal = gC0 * (T * r2.x - (Cf0 - Ca0) * inv) + gC1 * (T * r2.y - (Cf1 - Ca1) * inv) +
-                                    gC2 * (T * r2.z - (Cf2 - Ca2) * inv);
-                        dal += gD * (T * r2.w - (Df - Da) * inv);
-                        dal += gN0 * (T * r3.x - (Nf0 - Na0) * inv) + gN1 * (T * r3.y - (Nf1 - Na1) * inv) +
-                               gN2 * (T * r3.z - (Nf2 - Na2) * inv);
-                        dal += gA * Tend * inv;
-                        T = __fmul_rn(T, __fsub_rn(1.f, al));
-                        const float o = r1.w, hb = r1.z;
-                        float gG = 0.f;
-                        if (pe.alpha_raw < a.alpha_max) {
-                            g[5] = dal * pe.G;
-                            gG = dal * o;
+                    for (int q = 0; q < 16; ++q) g[q] = 0.f;
+                    bool contrib = false;
+                    if (base + j < lp) {
+                        const float4 r0 = s_rec[4 * j], r1 = s_rec[4 * j + 1];
+                        const float dx = fpx - r0.x, dy = fpy - r0.y;
+                        PairEval pe;
+                        if (eval_pair(dx, dy, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, a.alpha_max, a.alpha_min, pe)) {
+                            contrib = true;
+                            const float4 r2 = s_rec[4 * j + 2], r3 = s_rec[4 * j + 3];
+                            const float al = pe.alpha;
+                            const float w = __fmul_rn(al, T);
+                            Ca0 = __fmaf_rn(w, r2.x, Ca0);
+                            Ca1 = __fmaf_rn(w, r2.y, Ca1);
+                            Ca2 = __fmaf_rn(w, r2.z, Ca2);
+                            Da = __fmaf_rn(w, r2.w, Da);
+                            Na0 = __fmaf_rn(w, r3.x, Na0);
+                            Na1 = __fmaf_rn(w, r3.y, Na1);
+                            Na2 = __fmaf_rn(w, r3.z, Na2);
+                            const float inv = 1.f / (1.f - al);
+                            float dal = gC0 * (T * r2.x - (Cf0 - Ca0) * inv) + gC1 * (T * r2.y - (Cf1 - Ca1) * inv) +
+                                        gC2 * (T * r2.z - (Cf2 - Ca2) * inv);
+                            dal += gD * (T * r2.w - (Df - Da) * inv);
+                            dal += gN0 * (T * r3.x - (Nf0 - Na0) * inv) + gN1 * (T * r3.y - (Nf1 - Na1) * inv) +
+                                   gN2 * (T * r3.z - (Nf2 - Na2) * inv);
+                            dal += gA * Tend * inv;
+                            T = __fmul_rn(T, __fsub_rn(1.f, al));
+                            const float o = r1.w, hb = r1.z;
+                            float gG = 0.f;
+                            if (pe.alpha_raw < a.alpha_max) {
+                                g[5] = dal * pe.G;
+                                gG = dal * o;
+                            }
+                            float dGdQ = 0.f, dGdb = 0.f;
+                            if (pe.Q > 0.f) {
+                                dGdQ = -0.5f * hb * __fdividef(pe.p, pe.Q) * pe.G;
+                                dGdb = -0.25f * pe.p * (lg2_approx(pe.Q) * ln2) * pe.G;
+                            }
+                            const float gQ = gG * dGdQ;
+                            const float a2 = r0.z + r0.z, b2 = r0.w, c2 = r1.x + r1.x;
+                            g[0] = -gQ * (a2 * dx + b2 * dy);
+                            g[1] = -gQ * (b2 * dx + c2 * dy);
+                            g[2] = gQ * dx * dx;
+                            g[3] = gQ * 2.f * dx * dy;
+                            g[4] = gQ * dy * dy;
+                            g[6] = gG * dGdb;
+                            g[7] = gD * w;
+                            g[8] = gC0 * w;
+                            g[9] = gC1 * w;
+                            g[10] = gC2 * w;
+                            g[12] = gN0 * w;
+                            g[13] = gN1 * w;
+                            g[14] = gN2 * w;
                         }
-                        float dGdQ = 0.f, dGdb = 0.f;
-                        if (pe.Q > 0.f) {
-                            dGdQ = -0.5f * hb * __fdividef(pe.p, pe.Q) * pe.G;
-                            dGdb = -0.25f * pe.p * (lg2_approx(pe.Q) * ln2) * pe.G;
-                        }
-                        const float gQ = gG * dGdQ;
-                        const float a2 = r0.z + r0.z, b2 = r0.w, c2 = r1.x + r1.x;
-                        g[0] = -gQ * (a2 * dx + b2 * dy);
-                        g[1] = -gQ * (b2 * dx + c2 * dy);
-                        g[2] = gQ * dx * dx;
-                        g[3] = gQ * 2.f * dx * dy;
-                        g[4] = gQ * dy * dy;
-                        g[6] = gG * dGdb;
-                        g[7] = gD * w;
-                        g[8] = gC0 * w;
-                        g[9] = gC1 * w;
-                        g[10] = gC2 * w;
-                        g[12] = gN0 * w;
-                        g[13] = gN1 * w;
-                        g[14] = gN2 * w;
                     }
-                }
-                if (__any_sync(0xffffffffu, contrib)) {
-                    const float s = warp_reduce16(g, lane);
-                    if ((lane & 1) == 0) atomicAdd(a.g2d + 16 * (size_t)s_ent[j] + (lane >> 1), s);
+                    if (__any_sync(0xffffffffu, contrib)) {
+                        const float sum = warp_reduce16(g, lane);
+                        if ((lane & 1) == 0) atomicAdd(a.g2d + 16 * (size_t)s_ent[j] + (lane >> 1), sum);
+                    }
                 }
             }
         }
     }
 }
 
+static size_t fwd_smem(int batch) { return (size_t)batch * (64 + 4 * kCullFields); }
+static size_t bwd_smem(int batch) { return (size_t)batch * (64 + 4 * kCullFields + 4); }
+
 template <int TW, int TH>
 static cudaError_t launch_fwd_t(const FwdArgs &a, int grid, cudaStream_t s) {
-    const size_t smem = (size_t)a.batch * 64;
+    const size_t smem = fwd_smem(a.batch);
     k_render_fwd<TW, TH><<<grid, TW * TH, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int TW, int TH>
 static cudaError_t launch_bwd_t(const BwdArgs &a, int grid, cudaStream_t s) {
-    const size_t smem = (size_t)a.batch * 68;
+    const size_t smem = bwd_smem(a.batch);
     k_render_bwd<TW, TH><<<grid, TW * TH, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -308,9 +379,9 @@ static int persistent_grid(bool bwd, int batch) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (bwd)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_bwd<TW, TH>, TW * TH, (size_t)batch * 68);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_bwd<TW, TH>, TW * TH, bwd_smem(batch));
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_fwd<TW, TH>, TW * TH, (size_t)batch * 64);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_fwd<TW, TH>, TW * TH, fwd_smem(batch));
     if (per < 1) per = 1;
     return sms * per;
 }

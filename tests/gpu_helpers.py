@@ -105,7 +105,7 @@ def oracle_upstream(rast, grads, v, pixels=None):
     return c, d, a, n
 
 
-def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=1e-3, floor=1e-2, rows=None):
+def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=1e-3, floor=0.25, rows=None):
     """Tensor-level relative L2 and elementwise |d| <= elem * max(|g|, floor * rms(g))."""
     rep = {}
     for k in ("g_pos_op", "g_lscale_beta", "g_quat", "g_color"):

@@ -75,7 +75,7 @@ def test_sizes_and_layout_are_consistent():
     cams = _cams([(128, 96), (33, 17)])
     n, nv = 1000, 2
     pb = api.ges_proj_bytes(n, nv)
-    assert pb >= 256 + n * nv * (64 + 16 + 64)
+    assert pb >= 256 + n * nv * (64 + 32 + 64)
     lay = api.ges_get_layout(n, nv, cams, cfg, 5000)
     assert lay.proj_bytes == pb
     assert lay.n_tiles == 8 * 6 + 3 * 2
