@@ -169,8 +169,10 @@ GES_API ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *
  * dX/dalpha_i = T_i x_i - (X - sum_{j<=i} w_j x_j) / (1 - alpha_i), and for the
  * alpha output T_final / (1 - alpha_i). Per-splat screen-space gradients are
  * summed across each warp before FP32 atomics into a per-entry accumulator
- * (g2d, 16 floats per entry: u, v, conic a, b, c, opacity, beta, z, r, g, b, -,
- * nx, ny, nz, -), which the chain rule of S1-S4 then takes back to the inputs.
+ * (g2d, 16 floats per entry: dL/du, dL/dv; dL/dSigma' as the symmetric-matrix
+ * gradient G00, G01, G11 (dL = G00 dS00 + 2 G01 dS01 + G11 dS11); opacity, beta,
+ * z, r, g, b, -, nx, ny, nz, -), which the chain rule of S1-S4 then takes back
+ * to the inputs.
  * Inputs: the forward's inputs, `proj`/`bins` as left by ges_bin, the forward's
  * color, depth, normal, t_final and last, and the upstream gradients (same
  * layouts as the outputs; any of g_color, g_depth, g_alpha, g_normal may be NULL
@@ -213,7 +215,8 @@ GES_API ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_came
  *                 z32 bits (uint32; 0xffffffff if not listed), hit mask over the
  *                 tile box (row-major; valid when the box has <= 32 tiles), box
  *                 origin tx0 | ty0 << 16, box size w | h << 16, 0
- *   proj.g2d      [n_views * n] x 16 float screen-space gradient accumulator
+ *   proj.g2d      [n_views * n] x 16 float screen-space gradient accumulator (see
+ *                 ges_render_bwd for the layout)
  *   bins.inst_tile / inst_entry  [n_instances] uint32, sorted by (tile, z32, entry)
  *   bins.ranges   [n_tiles] x 2 uint32 [start, end) per global tile (0, 0 if empty);
  *                 global tile = tile_base[view] + ty * tiles_x + tx

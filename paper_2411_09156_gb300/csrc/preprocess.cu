@@ -91,16 +91,29 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
             const float J00 = fx * iz, J02 = -fx * rx * iz, J11 = fy * iz, J12 = -fy * ry * iz;
             const float T00 = J00 * vm[0] + J02 * vm[8], T01 = J00 * vm[1] + J02 * vm[9], T02 = J00 * vm[2] + J02 * vm[10];
             const float T10 = J11 * vm[4] + J12 * vm[8], T11 = J11 * vm[5] + J12 * vm[9], T12 = J11 * vm[6] + J12 * vm[10];
-            float A = a.P.lowpass, B = 0.f, C = a.P.lowpass;
+            // Sigma' = sum_k d_k u_k u_k^T + h I. Its determinant by the Cauchy-Binet sum
+            // sum_{j<k} d_j d_k (u_j x u_k)^2 + h (A0 + C0) + h^2 has no cancellation, so the
+            // conic of a long thin splat keeps float32 relative accuracy.
+            float ux[3], uy[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const float ux = T00 * R[k] + T01 * R[3 + k] + T02 * R[6 + k];
-                const float uy = T10 * R[k] + T11 * R[3 + k] + T12 * R[6 + k];
-                A = fmaf(dk[k] * ux, ux, A);
-                B = fmaf(dk[k] * ux, uy, B);
-                C = fmaf(dk[k] * uy, uy, C);
+                ux[k] = T00 * R[k] + T01 * R[3 + k] + T02 * R[6 + k];
+                uy[k] = T10 * R[k] + T11 * R[3 + k] + T12 * R[6 + k];
             }
-            const float det = A * C - B * B;
+            float A0 = 0.f, B = 0.f, C0 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                A0 = fmaf(dk[k] * ux[k], ux[k], A0);
+                B = fmaf(dk[k] * ux[k], uy[k], B);
+                C0 = fmaf(dk[k] * uy[k], uy[k], C0);
+            }
+            const float x01 = ux[0] * uy[1] - uy[0] * ux[1];
+            const float x02 = ux[0] * uy[2] - uy[0] * ux[2];
+            const float x12 = ux[1] * uy[2] - uy[1] * ux[2];
+            const float h = a.P.lowpass;
+            const float A = A0 + h, C = C0 + h;
+            const float det = dk[0] * dk[1] * x01 * x01 + dk[0] * dk[2] * x02 * x02 + dk[1] * dk[2] * x12 * x12 +
+                              h * (A0 + C0) + h * h;
             const float idet = 1.f / det;
             const float ca = C * idet, cb = -B * idet, cc = A * idet;
             const float u = fx * tx * iz + a.V.cx[v];
@@ -230,8 +243,6 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
             g1.z == 0.f && g1.w == 0.f && g2.x == 0.f && g2.y == 0.f && g2.z == 0.f && g3.x == 0.f &&
             g3.y == 0.f && g3.z == 0.f)
             continue;
-        const float4 c0 = a.rec[4 * e + 0], c1 = a.rec[4 * e + 1];
-        const float ca = c0.z, cb = c0.w, cc = c1.x;
         const float *vm = a.V.vm[v];
         const float tx = vm[0] * po.x + vm[1] * po.y + vm[2] * po.z + vm[3];
         const float ty = vm[4] * po.x + vm[5] * po.y + vm[6] * po.z + vm[7];
@@ -246,12 +257,8 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
         const float J00 = fx * iz, J02 = -fx * rx * iz, J11 = fy * iz, J12 = -fy * ry * iz;
         const float T[6] = {J00 * vm[0] + J02 * vm[8], J00 * vm[1] + J02 * vm[9], J00 * vm[2] + J02 * vm[10],
                             J11 * vm[4] + J12 * vm[8], J11 * vm[5] + J12 * vm[9], J11 * vm[6] + J12 * vm[10]};
-        // conic -> Sigma':  G_M = -C G_C C, G_C = [[ga, gb/2], [gb/2, gc]]
-        const float gA = g0.z, gB = 0.5f * g0.w, gC = g1.x;
-        const float t00 = gA * ca + gB * cb, t01 = gA * cb + gB * cc;
-        const float t10 = gB * ca + gC * cb, t11 = gB * cb + gC * cc;
-        const float M00 = -(ca * t00 + cb * t10), M01 = -(ca * t01 + cb * t11);
-        const float M11 = -(cb * t01 + cc * t11);
+        // dL/dSigma' (symmetric-matrix gradient) as accumulated by the render backward
+        const float M00 = g0.z, M01 = g0.w, M11 = g1.x;
         // Sigma' = sum_k s'_k^2 u_k u_k^T + h I with u_k = T r_k. With w_k = G_M u_k:
         //   dL/d(s'_k^2) += u_k . w_k,  dL/dR[:, k] += 2 s'_k^2 T^T w_k,
         //   dL/dT = 2 sum_k s'_k^2 w_k r_k^T

@@ -329,13 +329,16 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
                                 dGdQ = -0.5f * hb * __fdividef(pe.p, pe.Q) * pe.G;
                                 dGdb = -0.25f * pe.p * (lg2_approx(pe.Q) * ln2) * pe.G;
                             }
+                            // Q = d^T C d with C = Sigma'^-1 and d = pixel - mean; with m = C d:
+                            // dQ/dmean = -2 m and dQ/dSigma' = -m m^T (accumulated directly:
+                            // going through the conic gradient would cancel for thin splats)
                             const float gQ = gG * dGdQ;
-                            const float a2 = r0.z + r0.z, b2 = r0.w, c2 = r1.x + r1.x;
-                            g[0] = -gQ * (a2 * dx + b2 * dy);
-                            g[1] = -gQ * (b2 * dx + c2 * dy);
-                            g[2] = gQ * dx * dx;
-                            g[3] = gQ * 2.f * dx * dy;
-                            g[4] = gQ * dy * dy;
+                            const float mx = fmaf(r0.z, dx, 0.5f * r0.w * dy), my = fmaf(0.5f * r0.w, dx, r1.x * dy);
+                            g[0] = -2.f * gQ * mx;
+                            g[1] = -2.f * gQ * my;
+                            g[2] = -gQ * mx * mx;
+                            g[3] = -gQ * mx * my;
+                            g[4] = -gQ * my * my;
                             g[6] = gG * dGdb;
                             g[7] = gD * w;
                             g[8] = gC0 * w;

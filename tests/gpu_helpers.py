@@ -121,3 +121,19 @@ def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=1e-3, floor=0.2
         assert r <= rel_l2, (k, rep[k])
         assert bad.sum() == 0, (k, rep[k])
     return rep
+
+
+def oracle_g2d_sigma(g2d, conic):
+    """The oracle's screen-space gradient with its conic columns (a, b, c) mapped to the
+    gradient w.r.t. Sigma' (G = -C G_C C, symmetric entries 00, 01, 11), in FP64, the
+    layout the CUDA path accumulates."""
+    out = np.array(g2d, np.float64, copy=True)
+    a, b, c = conic[:, 0], conic[:, 1], conic[:, 2]
+    ga, gb, gc = g2d[:, 2], 0.5 * g2d[:, 3], g2d[:, 4]
+    # C G_C C for symmetric 2x2 C = [[a, b], [b, c]], G_C = [[ga, gb], [gb, gc]]
+    t00, t01 = ga * a + gb * b, ga * b + gb * c
+    t10, t11 = gb * a + gc * b, gb * b + gc * c
+    out[:, 2] = -(a * t00 + b * t10)
+    out[:, 3] = -(a * t01 + b * t11)
+    out[:, 4] = -(b * t01 + c * t11)
+    return out
