@@ -26,7 +26,8 @@ _LIB = os.path.join(_BUILD, "libges_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-FLAG_SUPPORT, FLAG_ALPHA_MIN, FLAG_T_MIN, FLAG_FACING = 1, 2, 4, 8
+FLAG_SUPPORT, FLAG_ALPHA_MIN, FLAG_T_MIN, FLAG_FACING, FLAG_CUSP = 1, 2, 4, 8, 16
+DECISION_FLAGS = FLAG_SUPPORT | FLAG_ALPHA_MIN | FLAG_T_MIN | FLAG_FACING
 
 
 def build_oracle(force: bool = False) -> str:

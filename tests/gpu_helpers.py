@@ -47,8 +47,10 @@ def compare_forward(rast, scene, cams, cfg, v=0, pixels=None, atol=IMG_ATOL):
     if pixels is not None:
         idx = np.asarray(pixels)[:, 1] * w + np.asarray(pixels)[:, 0]
         got = {k: a[idx] for k, a in got.items()}
-    mask = ref["flags"] == 0
-    rep = {"flagged": int((~mask).sum()), "pixels": int(mask.size)}
+    # image values are compared wherever no threshold decision is borderline; gradients
+    # (see grad_mask) also skip the centre-cusp pixels of beta < 2 splats
+    mask = (ref["flags"] & O.DECISION_FLAGS) == 0
+    rep = {"flagged": int((~mask).sum()), "pixels": int(mask.size), "cusp": int(((ref["flags"] & O.FLAG_CUSP) != 0).sum())}
     for k in ("color", "depth", "alpha", "normal"):
         err = np.abs(got[k][mask] - ref[k][mask])
         rep[k] = float(err.max()) if err.size else 0.0
@@ -62,6 +64,11 @@ def compare_forward(rast, scene, cams, cfg, v=0, pixels=None, atol=IMG_ATOL):
     ids[has] = ent[got["last"][has] - 1] % scene.n
     np.testing.assert_array_equal(ids[mask], ref["last_id"][mask])
     return rep, ref, mask
+
+
+def grad_mask(ref):
+    """Pixels whose upstream gradient is kept on both sides: no borderline decision, no cusp."""
+    return ref["flags"] == 0
 
 
 def upstream(rast, seed):

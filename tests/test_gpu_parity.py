@@ -126,8 +126,8 @@ def test_backward_matches_oracle_gradient(sh_degree):
         cams = [look_at((0.5, -2.2, 0.7), (0, 0, 0), 96, 80)]
     cfg = api.GESConfig(sh_degree=sh_degree, bg=(0.1, 0.2, 0.3))
     rast, t = H.gpu_forward(sc, cams, cfg)
-    rep, ref, mask = H.compare_forward(rast, sc, cams, cfg)
-    ups = H.mask_upstream(rast, H.upstream(rast, 1000), [mask])
+    rep, ref, _ = H.compare_forward(rast, sc, cams, cfg)
+    ups = H.mask_upstream(rast, H.upstream(rast, 1000), [H.grad_mask(ref)])
     g2d = torch.empty(sc.n * 16, dtype=torch.float32, device="cuda")
     grads = rast.backward(*t, *ups, g2d=g2d)
     torch.cuda.synchronize()
@@ -231,10 +231,10 @@ def test_full_size_scene_1p5m_sampled_fwd_bwd():
     cfg = api.GESConfig(sh_degree=3)
     rast, t = H.gpu_forward(sc, cams, cfg)
     px = _sample_pixels(np.random.default_rng(0), 1600, 1040, 192)
-    rep, ref, mask = H.compare_forward(rast, sc, cams, cfg, pixels=px)
+    rep, ref, _ = H.compare_forward(rast, sc, cams, cfg, pixels=px)
     assert rep["flagged"] <= 4
     keep = np.zeros(1600 * 1040, bool)
-    keep[(px[:, 1] * 1600 + px[:, 0])[mask]] = True
+    keep[(px[:, 1] * 1600 + px[:, 0])[H.grad_mask(ref)]] = True
     ups = H.mask_upstream(rast, H.upstream(rast, 1003), [keep])
     grads = rast.backward(*t, *ups)
     torch.cuda.synchronize()
