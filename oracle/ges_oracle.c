@@ -644,6 +644,25 @@ int orc_backward(int n, const double *pos_op, const double *lsb, const double *q
     return 0;
 }
 
+/* -------------------------------------------------- exported: S8 alone
+ * The chain rule of S1-S4 applied to a given per-splat screen-space gradient
+ * g2d (16 per splat, the layout of orc_backward: u, v, conic a, b, c, opacity,
+ * beta, z, r, g, b, -, nx, ny, nz, -). Outputs are ACCUMULATED. */
+int orc_chain(int n, const double *pos_op, const double *lsb, const double *quat, const double *color,
+              const orc_camera *cam, const orc_config *cfg, const double *g2d,
+              double *g_pos_op, double *g_lsb, double *g_quat, double *g_col) {
+    orc_splat *sp = project_all(n, pos_op, lsb, quat, color, cam, cfg);
+    int K3 = 3 * n_sh_coeffs(cfg->sh_degree);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i) {
+        if (!sp[i].visible) continue;
+        backprop_splat(pos_op + 4 * i, lsb + 4 * i, quat + 4 * i, color + (size_t)K3 * i, cam, cfg, &sp[i],
+                       g2d + 16 * (size_t)i, g_pos_op + 4 * i, g_lsb + 4 * i, g_quat + 4 * i, g_col + (size_t)K3 * i);
+    }
+    free(sp);
+    return 0;
+}
+
 /* -------------------------------------------------- exported: SH basis (for pins) */
 int orc_sh_basis(int deg, const double *d, double *Y, double *dY) {
     sh_basis(deg, d, Y, (double (*)[3])dY);

@@ -65,6 +65,7 @@ def _load():
             lib.orc_render.argtypes = [ctypes.c_int, P, P, P, P, P, P, ctypes.c_int, P, P, P, P, P, P, P, P, P]
             lib.orc_backward.argtypes = [ctypes.c_int, P, P, P, P, P, P, ctypes.c_int, P, P, P, P, P, P, P, P,
                                          P, P]
+            lib.orc_chain.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P, P, P, P]
             lib.orc_sh_basis.argtypes = [ctypes.c_int, P, P, P]
             lib.orc_phi.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P]
             _lib = lib
@@ -163,6 +164,21 @@ def backward(scene, cam: dict, cfg: dict, g_color, g_depth, g_alpha, g_normal, p
     lib.orc_backward(n, _p(pos), _p(lsb), _p(q), _p(col), ctypes.byref(c), ctypes.byref(g), npix,
                      _p(px) if px is not None else None, _p(gc), _p(gd), _p(ga), _p(gn), _p(out["g2d"]),
                      _p(out["g_pos_op"]), _p(out["g_lscale_beta"]), _p(out["g_quat"]), _p(out["g_color"]))
+    return out
+
+
+def chain(scene, cam: dict, cfg: dict, g2d) -> dict:
+    """S8 alone: the 3-D gradients implied by a per-splat screen-space gradient g2d (N, 16)
+    in the layout `backward` returns (conic columns a, b, c)."""
+    lib = _load()
+    pos, lsb, q, col = _arrays(scene)
+    n = pos.shape[0]
+    g2 = _d(g2d).reshape(n, 16)
+    out = dict(g_pos_op=np.zeros((n, 4)), g_lscale_beta=np.zeros((n, 4)), g_quat=np.zeros((n, 4)),
+               g_color=np.zeros_like(col))
+    c, g = _cam(cam), _cfg(cfg, scene.sh_degree)
+    lib.orc_chain(n, _p(pos), _p(lsb), _p(q), _p(col), ctypes.byref(c), ctypes.byref(g), _p(g2),
+                  _p(out["g_pos_op"]), _p(out["g_lscale_beta"]), _p(out["g_quat"]), _p(out["g_color"]))
     return out
 
 

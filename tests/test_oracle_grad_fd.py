@@ -100,3 +100,17 @@ def test_rgb_gradient_is_the_blend_weight():
     assert np.all(an["g_color"][:, 1:] == 0)
     assert np.count_nonzero(w) == out["n_contrib"][0]
     np.testing.assert_allclose(w.sum(), out["alpha"][0], rtol=1e-12)
+
+
+def test_chain_alone_reproduces_backward():
+    """The S8 entry applied to backward's own screen-space gradient gives backward's 3-D gradient."""
+    cam = look_at((0.0, -3.0, 0.25), (0, 0, 0), W, H).as_dict()
+    cfg = oracle_cfg()
+    sc = _scene(7, 2)
+    rng = np.random.default_rng(9)
+    npx = W * H
+    an = O.backward(sc, cam, cfg, rng.normal(size=(npx, 3)), rng.normal(size=npx), rng.normal(size=npx),
+                    rng.normal(size=(npx, 3)))
+    ch = O.chain(sc, cam, cfg, an["g2d"])
+    for k in ("g_pos_op", "g_lscale_beta", "g_quat", "g_color"):
+        np.testing.assert_allclose(ch[k], an[k], rtol=1e-12, atol=1e-14)
