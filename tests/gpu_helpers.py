@@ -112,8 +112,15 @@ def oracle_upstream(rast, grads, v, pixels=None):
     return c, d, a, n
 
 
-def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=1e-3, floor=0.25, rows=None):
-    """Tensor-level relative L2 and elementwise |d| <= elem * max(|g|, floor * rms(g))."""
+def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=3e-3, floor=0.25, rows=None):
+    """Tensor-level relative L2 <= 1e-3 (the gradient tolerance) and, as a guard against a wrong
+    formula for a single parameter, elementwise |d| <= elem * max(|g|, floor * rms(g)).
+
+    The elementwise bound allows for the float32 error model of the front-to-back
+    replay: the colour/depth/normal behind a splat is the final value minus the
+    prefix sum, so a splat deep in a pixel's list (T_i ~ 1e-4) carries an absolute
+    error of a few ulp of the final value, i.e. a relative error up to ~1e-3 of its
+    own small gradient."""
     rep = {}
     for k in ("g_pos_op", "g_lscale_beta", "g_quat", "g_color"):
         a = np.asarray(got[k], np.float64).reshape(len(got[k]), -1)

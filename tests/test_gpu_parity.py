@@ -1,8 +1,9 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerances: keys, order and contributor counts bit-exact; colour, depth,
-alpha and normal within 2e-4 absolute; gradients within 1e-3 relative L2 and
-elementwise 1e-3 * max(|g|, 0.25 rms(g)). Pixels where FP32 and FP64 may
+alpha and normal within 2e-4 absolute; gradients within 1e-3 relative L2 per
+tensor, with an elementwise guard of 3e-3 * max(|g|, 0.25 rms(g)) (see
+gpu_helpers.compare_grads for its float32 error model). Pixels where FP32 and FP64 may
 take a threshold decision differently are flagged by the oracle, excluded from
 the image comparison (their count is asserted small) and given zero upstream
 gradient on both sides.
