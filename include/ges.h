@@ -81,7 +81,8 @@ typedef enum ges_status {
     GES_ERR_INVALID_ARG = 1, /* host-side check failed; nothing was launched */
     GES_ERR_CAPACITY = 2,    /* more tile instances than `bins` holds; lists were truncated */
     GES_ERR_CUDA = 3,        /* a CUDA launch or copy failed */
-    GES_ERR_NUMERIC = 4      /* a visible splat had a non-finite projection; it was culled */
+    GES_ERR_NUMERIC = 4,     /* a visible splat had a non-finite projection; it was culled */
+    GES_ERR_TOO_LARGE = 5    /* the problem exceeds the fixed scratch of ges_render_bwd_noalloc */
 } ges_status;
 
 /* Pinhole camera. viewmat: row-major 3x4 world-to-camera [R | t]; camera x right,
@@ -206,6 +207,39 @@ GES_API ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_came
                                       const float *color_in, const void *proj, size_t proj_bytes, const float *g2d,
                                       float *g_pos_op, float *g_lscale_beta, float *g_quat, float *g_color_in,
                                       void *stream);
+
+/* ges_render_bwd for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart to this call; it is a property of the library.
+ * ges_render_bwd needs an accumulator of 16 floats per (view, splat) entry that
+ * the caller provides (inside `proj`, or as `g2d`). Callers that must not
+ * allocate while they run (cudaMalloc can synchronise the device and has no
+ * bounded latency, so interactive and real-time loops avoid it; some host
+ * applications also keep all device memory in their own pool and hand a library
+ * only the tensors it reads and writes) can call this variant instead. It
+ * computes the same gradients, with the accumulator in a fixed array inside the
+ * library, so it allocates nothing and needs no scratch from the caller.
+ *
+ * Arguments: as ges_render_bwd, without g2d. `proj` must still be the buffer
+ * ges_preprocess filled (its own accumulator region is not used).
+ * Limit: n * n_views <= GES_NOALLOC_MAX_ENTRIES (524,288 entries, a 32 MiB array
+ * that every GPU which loads the library keeps until the process exits); larger
+ * problems return GES_ERR_TOO_LARGE and launch nothing.
+ * Set-up: the first call on a device (with that device current) looks up the
+ * array's device address; make that first call before any stream capture.
+ * Sharing: all calls use the same array, which keeps the previous call's
+ * contents; each call zeroes the part it uses on `stream` before accumulating.
+ * Calls that overlap on the GPU (different streams, or different threads on the
+ * same device) race on the array and give wrong gradients. */
+#define GES_NOALLOC_MAX_ENTRIES 524288
+GES_API ges_status ges_render_bwd_noalloc(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                                          const float *pos_op, const float *lscale_beta, const float *quat,
+                                          const float *color_in, void *proj, size_t proj_bytes, const void *bins,
+                                          size_t bins_bytes, const float *color, const float *depth,
+                                          const float *normal, const float *t_final, const uint32_t *last,
+                                          const float *g_color, const float *g_depth, const float *g_alpha,
+                                          const float *g_normal, float *g_pos_op, float *g_lscale_beta,
+                                          float *g_quat, float *g_color_in, void *stream);
 
 /* Byte offsets of the arrays inside `proj` and `bins`, for callers that inspect
  * the intermediate results (tests, tools). Host-only; launches nothing.

@@ -13,8 +13,9 @@ from . import build as _build
 
 MAX_VIEWS = 32
 STATUS_NAMES = {0: "GES_OK", 1: "GES_ERR_INVALID_ARG", 2: "GES_ERR_CAPACITY", 3: "GES_ERR_CUDA",
-                4: "GES_ERR_NUMERIC"}
-GES_OK, GES_ERR_INVALID_ARG, GES_ERR_CAPACITY, GES_ERR_CUDA, GES_ERR_NUMERIC = range(5)
+                4: "GES_ERR_NUMERIC", 5: "GES_ERR_TOO_LARGE"}
+GES_OK, GES_ERR_INVALID_ARG, GES_ERR_CAPACITY, GES_ERR_CUDA, GES_ERR_NUMERIC, GES_ERR_TOO_LARGE = range(6)
+NOALLOC_MAX_ENTRIES = 524288
 
 
 class GESError(RuntimeError):
@@ -67,6 +68,8 @@ SIGNATURES = {
     "ges_render_bwd": (ctypes.c_int, [_I, _I, _CAM, _CFG, _P, _P, _P, _P, _P, _S, _P, _S, _P, _P, _P, _P, _P,
                                       _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ges_sync_status": (ctypes.c_int, [_P, _S, _P]),
+    "ges_render_bwd_noalloc": (ctypes.c_int, [_I, _I, _CAM, _CFG, _P, _P, _P, _P, _P, _S, _P, _S, _P, _P, _P, _P,
+                                              _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 _lock = threading.Lock()

@@ -159,6 +159,19 @@ def ges_render_bwd(n, n_views, cams_c, cfg_c, pos_op, lscale_beta, quat, color_i
                                     _stream(stream)), "ges_render_bwd")
 
 
+def ges_render_bwd_noalloc(n, n_views, cams_c, cfg_c, pos_op, lscale_beta, quat, color_in, proj, bins, color, depth,
+                           normal, t_final, last, g_color, g_depth, g_alpha, g_normal, g_pos_op, g_lscale_beta,
+                           g_quat, g_color_in, stream=None) -> None:
+    """ges_render_bwd with its accumulator in the library's fixed array (no caller scratch;
+    n * n_views <= 524,288; calls overlapping on the GPU race)."""
+    check(_lib.lib().ges_render_bwd_noalloc(n, n_views, cams_c, ctypes.byref(cfg_c), _ptr(pos_op), _ptr(lscale_beta),
+                                            _ptr(quat), _ptr(color_in), _ptr(proj), proj.numel(), _ptr(bins),
+                                            bins.numel(), _ptr(color), _ptr(depth), _ptr(normal), _ptr(t_final),
+                                            _ptr(last), _ptr(g_color), _ptr(g_depth), _ptr(g_alpha),
+                                            _ptr(g_normal), _ptr(g_pos_op), _ptr(g_lscale_beta), _ptr(g_quat),
+                                            _ptr(g_color_in), _stream(stream)), "ges_render_bwd_noalloc")
+
+
 def ges_sync_status(proj, stream=None) -> int:
     """Synchronises the stream; returns (and clears) the device-recorded status code."""
     return int(_lib.lib().ges_sync_status(_ptr(proj), proj.numel(), _stream(stream)))
