@@ -99,7 +99,8 @@ typedef struct ges_camera {
  * alpha_max 0.99, t_min 1e-4, jac_clamp 1.3. */
 typedef struct ges_config {
     int32_t tile_w, tile_h; /* 16x16, 8x8 or 32x8 */
-    int32_t batch;          /* splat records staged in shared memory per round: 32..256, multiple of 32 */
+    int32_t batch;          /* render: list entries each warp prefetches ahead of the 32 it evaluates
+                               (32..256, multiple of 32) */
     int32_t sh_degree;      /* -1 (RGB given) or 0..3 */
     int32_t phi_mode;       /* 0 off, 1 centred (default), 2 as printed in Eq. 7 */
     float rho;              /* shape strength of Eq. 7 (0.1, Sec. 4.2) */
@@ -107,7 +108,8 @@ typedef struct ges_config {
     float alpha_min, alpha_max, t_min;
     float jac_clamp;        /* |X/Z| is clamped to jac_clamp * (W/2)/fx in J (likewise y) */
     float bg[3];            /* background colour */
-    int32_t persistent;     /* 0: one CTA per tile; 1: persistent CTAs over a longest-first tile queue */
+    int32_t persistent;     /* 0: one CTA per tile; 1: persistent warps taking (tile, 8x4 block) items of a
+                               longest-first tile queue */
 } ges_config;
 
 /* Number of bytes `proj` must hold for n splats and n_views views:

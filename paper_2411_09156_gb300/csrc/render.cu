@@ -1,11 +1,16 @@
 // S6 forward compositing and S7 backward replay.
 //
-// One CTA renders one tile (one thread per pixel). The tile's depth-sorted list
-// is walked in batches: each batch of splat records is gathered into shared
-// memory by the whole CTA, then every pixel evaluates the batch from shared
-// memory. A pixel stops at the transmittance cutoff; a warp leaves a batch when
-// all its lanes are done, and the CTA stops fetching batches once
-// __syncthreads_count reports no live pixel.
+// One CTA per tile (persistent CTAs take tiles from a longest-first queue). Each
+// warp owns a compact 8x4 block of the tile's pixels and walks the tile's
+// depth-sorted list on its own, 32 entries at a time: every lane loads one
+// record, tests whether that splat's support can reach any pixel of the warp's
+// block (the exact ellipse-rectangle test of the binning, with a margin), and the
+// warp then evaluates only the splats that can (ballot + find-first-set), reading
+// them from a per-warp shared-memory slot. Warps never wait for each other: a
+// warp stops as soon as its own pixels reach the transmittance cutoff (forward)
+// or its last contributor (backward), and the records shared by the warps of a
+// tile are served from L1/L2. Each warp prefetches the records `batch` entries
+// ahead of the chunk it evaluates into L2.
 //
 // The backward replays the list front to back from the stored t_final and
 // `last` (no per-pixel lists), and reduces each splat's 16 gradient values
@@ -16,21 +21,24 @@
 
 namespace ges {
 
-
-
-__device__ __forceinline__ bool next_tile(const uint32_t *queue, uint32_t *counter, uint32_t n_tiles, int it,
-                                          uint32_t *s_item, uint32_t &tile) {
+// Next work item of a warp: a tile and the 8x4 sub-block of it that the warp
+// renders. Plain launch: CTA = tile, warp w takes sub-block w. Persistent launch:
+// each warp takes the next (tile, sub-block) item of the longest-first queue with
+// its own atomic, so no warp waits for another.
+__device__ __forceinline__ bool next_item(const uint32_t *queue, uint32_t *counter, uint32_t n_tiles, int nw, int it,
+                                          int warp, int lane, uint32_t &tile, int &sb) {
     if (queue) {
-        if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1u);
-        __syncthreads();
-        const uint32_t item = *s_item;
-        __syncthreads();
-        if (item >= n_tiles) return false;
-        tile = queue[item];
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_tiles * (uint32_t)nw) return false;
+        tile = queue[item / (uint32_t)nw];
+        sb = (int)(item % (uint32_t)nw);
         return true;
     }
     if (it > 0) return false;
     tile = blockIdx.x;
+    sb = warp;
     return true;
 }
 
@@ -40,56 +48,39 @@ __device__ __forceinline__ int view_of_tile(const ViewSet &V, uint32_t tile) {
     return v;
 }
 
-// Warp footprint inside a tile: 8 x 4 pixels, so that a warp's pixels are
-// compact and a splat can be culled for the whole warp at once.
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+constexpr uint32_t kNone = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t entry_or_none(const uint32_t *inst_entry, uint32_t idx, uint32_t end) {
+    return idx < end ? __ldg(inst_entry + idx) : kNone;
+}
+
+// Warp footprint inside a tile: 8 x 4 pixels.
 constexpr int kWarpW = 8, kWarpH = 4;
 
 template <int TW>
-__device__ __forceinline__ void warp_pixel(int tid, int &lx, int &ly, int &wx0, int &wy0) {
+__device__ __forceinline__ void warp_pixel(int sb, int lane, int &lx, int &ly, int &wx0, int &wy0) {
     constexpr int WPR = TW / kWarpW;
-    const int warp = tid >> 5, lane = tid & 31;
-    wx0 = (warp % WPR) * kWarpW;
-    wy0 = (warp / WPR) * kWarpH;
+    wx0 = (sb % WPR) * kWarpW;
+    wy0 = (sb / WPR) * kWarpH;
     lx = wx0 + (lane & 7);
     ly = wy0 + (lane >> 3);
 }
 
-// Culling fields of a staged batch, structure-of-arrays so that 32 lanes testing
-// 32 splats read consecutive words: u, v, a, b, c, q_cut (1 + 2^-10), 1/a, 1/c.
-constexpr int kCullFields = 8;
-
-__device__ __forceinline__ void stage_record(const float4 *rec, uint32_t e, uint32_t k, int batch, float4 *s_rec,
-                                             float *s_cull) {
-    const float4 *r = rec + 4 * (size_t)e;
-    float4 r0 = r[0];
-    const float4 r1 = r[1];
-    s_cull[0 * batch + k] = r0.x;
-    s_cull[1 * batch + k] = r0.y;
-    s_cull[2 * batch + k] = r0.z;
-    s_cull[3 * batch + k] = r0.w;
-    s_cull[4 * batch + k] = r1.x;
-    s_cull[5 * batch + k] = r1.y * kSupportMargin;
-    s_cull[6 * batch + k] = 1.f / r0.z;
-    s_cull[7 * batch + k] = 1.f / r1.x;
-    r0.w = r0.w + r0.w;  // 2b for the pair evaluation
-    s_rec[4 * k + 0] = r0;
-    s_rec[4 * k + 1] = r1;
-    s_rec[4 * k + 2] = r[2];
-    s_rec[4 * k + 3] = r[3];
-}
-
-// Can the support Q <= q_cut of staged splat j reach the rectangle of pixel
-// centres [rx0, rx1] x [ry0, ry1]? Minimum of the convex Q over the rectangle:
-// 0 if it holds the centre, else on an edge at the clamped 1-D minimiser.
-// Conservative: the margin on q_cut absorbs the rounding of this estimate.
-__device__ __forceinline__ bool warp_may_hit(const float *s_cull, int batch, uint32_t j, float rx0, float rx1,
-                                             float ry0, float ry1) {
-    const float u = s_cull[j], v = s_cull[batch + j];
-    const float a = s_cull[2 * batch + j], b = s_cull[3 * batch + j], c = s_cull[4 * batch + j];
-    const float qm = s_cull[5 * batch + j], ia = s_cull[6 * batch + j], ic = s_cull[7 * batch + j];
+// Can the support Q <= q_cut of a splat with centre (u, v) and conic (a, b, c)
+// reach the rectangle of pixel centres [rx0, rx1] x [ry0, ry1]? The minimum of
+// the convex Q over the rectangle is 0 if it holds the centre, else it lies on
+// an edge at the clamped 1-D minimiser. qm carries a margin (1 + 2^-10) that
+// absorbs the rounding of this estimate, so the test never drops a pixel that
+// the per-pixel evaluation would blend.
+__device__ __forceinline__ bool warp_may_hit(float u, float v, float a, float b, float c, float qm, float rx0,
+                                             float rx1, float ry0, float ry1) {
     const float X0 = rx0 - u, X1 = rx1 - u, Y0 = ry0 - v, Y1 = ry1 - v;
     if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
-    const float b2 = b + b;
+    const float ia = __frcp_rn(a), ic = __frcp_rn(c), b2 = b + b;
     auto q = [&](float X, float Y) { return fmaf(a * X, X, fmaf(b2 * X, Y, c * Y * Y)); };
     float best = q(X0, fminf(fmaxf(-b * X0 * ic, Y0), Y1));
     best = fminf(best, q(X1, fminf(fmaxf(-b * X1 * ic, Y0), Y1)));
@@ -98,17 +89,35 @@ __device__ __forceinline__ bool warp_may_hit(const float *s_cull, int batch, uin
     return best <= qm;
 }
 
+// Loads record e, tests it against the warp's block and, if it can contribute,
+// stores it (with 2b in place of b) into the warp's slot `lane`.
+__device__ __forceinline__ bool load_cull_stage(const float4 *rec, uint32_t e, float rx0, float rx1, float ry0,
+                                                float ry1, float4 (*slot)[4], int lane) {
+    if (e == kNone) return false;
+    const float4 *r = rec + 4 * (size_t)e;
+    float4 r0 = __ldg(r);
+    const float4 r1 = __ldg(r + 1);
+    if (!warp_may_hit(r0.x, r0.y, r0.z, r0.w, r1.x, r1.y * kSupportMargin, rx0, rx1, ry0, ry1)) return false;
+    r0.w = r0.w + r0.w;
+    slot[lane][0] = r0;
+    slot[lane][1] = r1;
+    slot[lane][2] = __ldg(r + 2);
+    slot[lane][3] = __ldg(r + 3);
+    return true;
+}
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
-    constexpr int NT = TW * TH;
-    extern __shared__ float4 s_rec[];  // [batch][4], then the culling fields [8][batch]
-    float *s_cull = reinterpret_cast<float *>(s_rec + 4 * a.batch);
-    __shared__ uint32_t s_item;
-    const int tid = threadIdx.x, lane = tid & 31;
-    int lx, ly, wx0, wy0;
-    warp_pixel<TW>(tid, lx, ly, wx0, wy0);
+    constexpr int NW = TW * TH / 32;
+    __shared__ float4 s_rec[NW][32][4];  // per-warp slot of the current chunk's records
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float4(*slot)[4] = s_rec[warp];
+    const uint32_t ahead = (uint32_t)a.batch;
     uint32_t tile;
-    for (int it = 0; next_tile(a.queue, a.counter, (uint32_t)a.V.n_tiles, it, &s_item, tile); ++it) {
+    int sb;
+    for (int it = 0; next_item(a.queue, a.counter, (uint32_t)a.V.n_tiles, NW, it, warp, lane, tile, sb); ++it) {
+        int lx, ly, wx0, wy0;
+        warp_pixel<TW>(sb, lane, lx, ly, wx0, wy0);
         const int v = view_of_tile(a.V, tile);
         const int lt = (int)tile - a.V.tile_base[v];
         const int tiles_x = a.V.tiles_x[v];
@@ -123,42 +132,42 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
         float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
         uint32_t cnt = 0, last = rg.x, stop = rg.y;
         bool done = !inside;
-        for (uint32_t base = rg.x; base < rg.y; base += (uint32_t)a.batch) {
-            if (__syncthreads_count(!done) == 0) break;
-            const uint32_t nb = min((uint32_t)a.batch, rg.y - base);
-            for (uint32_t k = tid; k < nb; k += NT) stage_record(a.rec, a.inst_entry[base + k], k, a.batch, s_rec, s_cull);
-            __syncthreads();
-            if (__all_sync(0xffffffffu, done)) continue;
-            for (uint32_t c0 = 0; c0 < nb; c0 += 32) {
-                const uint32_t jl = c0 + lane;
-                const bool hit = jl < nb && warp_may_hit(s_cull, a.batch, jl, rx0, rx1, ry0, ry1);
-                uint32_t mask = __ballot_sync(0xffffffffu, hit);
-                while (mask) {
-                    const uint32_t j = c0 + (uint32_t)(__ffs(mask) - 1);
-                    mask &= mask - 1;
-                    if (done) continue;
-                    const float4 r0 = s_rec[4 * j], r1 = s_rec[4 * j + 1];
-                    PairEval pe;
-                    if (!eval_pair(fpx - r0.x, fpy - r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, a.alpha_max,
-                                   a.alpha_min, pe))
-                        continue;
-                    const float Tn = __fmul_rn(T, __fsub_rn(1.f, pe.alpha));
-                    if (Tn < a.t_min) { done = true; stop = base + j + 1; continue; }
-                    const float w = __fmul_rn(pe.alpha, T);
-                    const float4 r2 = s_rec[4 * j + 2], r3 = s_rec[4 * j + 3];
-                    C0 = __fmaf_rn(w, r2.x, C0);
-                    C1 = __fmaf_rn(w, r2.y, C1);
-                    C2 = __fmaf_rn(w, r2.z, C2);
-                    D = __fmaf_rn(w, r2.w, D);
-                    N0 = __fmaf_rn(w, r3.x, N0);
-                    N1 = __fmaf_rn(w, r3.y, N1);
-                    N2 = __fmaf_rn(w, r3.z, N2);
-                    T = Tn;
-                    ++cnt;
-                    last = base + j + 1;
-                }
-                if (__all_sync(0xffffffffu, done)) break;
+        uint32_t e_cur = entry_or_none(a.inst_entry, rg.x + lane, rg.y);
+        uint32_t e_pf = entry_or_none(a.inst_entry, rg.x + ahead + lane, rg.y);
+        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += 32) {
+            if (__all_sync(0xffffffffu, done)) break;
+            if (e_pf != kNone) prefetch_l2(a.rec + 4 * (size_t)e_pf);
+            e_pf = entry_or_none(a.inst_entry, c0 + 32 + ahead + lane, rg.y);
+            const uint32_t e_nxt = entry_or_none(a.inst_entry, c0 + 32 + lane, rg.y);
+            const bool hit = load_cull_stage(a.rec, e_cur, rx0, rx1, ry0, ry1, slot, lane);
+            e_cur = e_nxt;
+            uint32_t mask = __ballot_sync(0xffffffffu, hit);
+            __syncwarp();
+            while (mask) {
+                const int bit = __ffs(mask) - 1;
+                mask &= mask - 1;
+                if (done) continue;
+                const float4 r0 = slot[bit][0], r1 = slot[bit][1];
+                PairEval pe;
+                if (!eval_pair(fpx - r0.x, fpy - r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, a.alpha_max, a.alpha_min,
+                               pe))
+                    continue;
+                const float Tn = __fmul_rn(T, __fsub_rn(1.f, pe.alpha));
+                if (Tn < a.t_min) { done = true; stop = c0 + (uint32_t)bit + 1; continue; }
+                const float w = __fmul_rn(pe.alpha, T);
+                const float4 r2 = slot[bit][2], r3 = slot[bit][3];
+                C0 = __fmaf_rn(w, r2.x, C0);
+                C1 = __fmaf_rn(w, r2.y, C1);
+                C2 = __fmaf_rn(w, r2.z, C2);
+                D = __fmaf_rn(w, r2.w, D);
+                N0 = __fmaf_rn(w, r3.x, N0);
+                N1 = __fmaf_rn(w, r3.y, N1);
+                N2 = __fmaf_rn(w, r3.z, N2);
+                T = Tn;
+                ++cnt;
+                last = c0 + (uint32_t)bit + 1;
             }
+            __syncwarp();
         }
         if (inside) {
             const long long P = (long long)W * H;
@@ -223,17 +232,19 @@ __device__ __forceinline__ float warp_reduce16(float (&g)[16], int lane) {
 
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
-    constexpr int NT = TW * TH;
-    extern __shared__ float4 s_rec[];  // [batch][4], culling fields [8][batch], entry ids [batch]
-    float *s_cull = reinterpret_cast<float *>(s_rec + 4 * a.batch);
-    uint32_t *s_ent = reinterpret_cast<uint32_t *>(s_cull + kCullFields * a.batch);
-    __shared__ uint32_t s_item, s_max;
-    const int tid = threadIdx.x, lane = tid & 31;
-    int lx, ly, wx0, wy0;
-    warp_pixel<TW>(tid, lx, ly, wx0, wy0);
+    constexpr int NW = TW * TH / 32;
+    __shared__ float4 s_rec[NW][32][4];
+    __shared__ uint32_t s_ent[NW][32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float4(*slot)[4] = s_rec[warp];
+    uint32_t *went = s_ent[warp];
+    const uint32_t ahead = (uint32_t)a.batch;
     const float ln2 = 0.69314718055994531f;
     uint32_t tile;
-    for (int it = 0; next_tile(a.queue, a.counter, (uint32_t)a.V.n_tiles, it, &s_item, tile); ++it) {
+    int sb;
+    for (int it = 0; next_item(a.queue, a.counter, (uint32_t)a.V.n_tiles, NW, it, warp, lane, tile, sb); ++it) {
+        int lx, ly, wx0, wy0;
+        warp_pixel<TW>(sb, lane, lx, ly, wx0, wy0);
         const int v = view_of_tile(a.V, tile);
         const int lt = (int)tile - a.V.tile_base[v];
         const int tiles_x = a.V.tiles_x[v];
@@ -267,112 +278,100 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
                 Nf0 = a.normal[c3]; Nf1 = a.normal[c3 + P]; Nf2 = a.normal[c3 + 2 * P];
             }
         }
-        if (tid == 0) s_max = rg.x;
-        __syncthreads();
-        if (lp > rg.x) atomicMax(&s_max, lp);
-        __syncthreads();
-        const uint32_t maxl = s_max;
+        const uint32_t wend = __reduce_max_sync(0xffffffffu, lp);  // this warp replays [rg.x, wend)
         float T = 1.f, Ca0 = 0.f, Ca1 = 0.f, Ca2 = 0.f, Da = 0.f, Na0 = 0.f, Na1 = 0.f, Na2 = 0.f;
-        for (uint32_t base = rg.x; base < maxl; base += (uint32_t)a.batch) {
-            __syncthreads();
-            const uint32_t nb = min((uint32_t)a.batch, maxl - base);
-            for (uint32_t k = tid; k < nb; k += NT) {
-                const uint32_t e = a.inst_entry[base + k];
-                stage_record(a.rec, e, k, a.batch, s_rec, s_cull);
-                s_ent[k] = e;
-            }
-            __syncthreads();
-            for (uint32_t c0 = 0; c0 < nb; c0 += 32) {
-                if (__all_sync(0xffffffffu, base + c0 >= lp)) break;
-                const uint32_t jl = c0 + lane;
-                const bool hit = jl < nb && warp_may_hit(s_cull, a.batch, jl, rx0, rx1, ry0, ry1);
-                uint32_t mask = __ballot_sync(0xffffffffu, hit);
-                while (mask) {
-                    const uint32_t j = c0 + (uint32_t)(__ffs(mask) - 1);
-                    mask &= mask - 1;
-                    float g[16];
+        uint32_t e_cur = entry_or_none(a.inst_entry, rg.x + lane, wend);
+        uint32_t e_pf = entry_or_none(a.inst_entry, rg.x + ahead + lane, wend);
+        for (uint32_t c0 = rg.x; c0 < wend; c0 += 32) {
+            if (e_pf != kNone) prefetch_l2(a.rec + 4 * (size_t)e_pf);
+            e_pf = entry_or_none(a.inst_entry, c0 + 32 + ahead + lane, wend);
+            const uint32_t e_nxt = entry_or_none(a.inst_entry, c0 + 32 + lane, wend);
+            const bool hit = load_cull_stage(a.rec, e_cur, rx0, rx1, ry0, ry1, slot, lane);
+            if (hit) went[lane] = e_cur;
+            e_cur = e_nxt;
+            uint32_t mask = __ballot_sync(0xffffffffu, hit);
+            __syncwarp();
+            while (mask) {
+                const int bit = __ffs(mask) - 1;
+                mask &= mask - 1;
+                float g[16];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) g[q] = 0.f;
-                    bool contrib = false;
-                    if (base + j < lp) {
-                        const float4 r0 = s_rec[4 * j], r1 = s_rec[4 * j + 1];
-                        const float dx = fpx - r0.x, dy = fpy - r0.y;
-                        PairEval pe;
-                        if (eval_pair(dx, dy, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, a.alpha_max, a.alpha_min, pe)) {
-                            contrib = true;
-                            const float4 r2 = s_rec[4 * j + 2], r3 = s_rec[4 * j + 3];
-                            const float al = pe.alpha;
-                            const float w = __fmul_rn(al, T);
-                            Ca0 = __fmaf_rn(w, r2.x, Ca0);
-                            Ca1 = __fmaf_rn(w, r2.y, Ca1);
-                            Ca2 = __fmaf_rn(w, r2.z, Ca2);
-                            Da = __fmaf_rn(w, r2.w, Da);
-                            Na0 = __fmaf_rn(w, r3.x, Na0);
-                            Na1 = __fmaf_rn(w, r3.y, Na1);
-                            Na2 = __fmaf_rn(w, r3.z, Na2);
-                            const float inv = 1.f / (1.f - al);
-                            float dal = gC0 * (T * r2.x - (Cf0 - Ca0) * inv) + gC1 * (T * r2.y - (Cf1 - Ca1) * inv) +
-                                        gC2 * (T * r2.z - (Cf2 - Ca2) * inv);
-                            dal += gD * (T * r2.w - (Df - Da) * inv);
-                            dal += gN0 * (T * r3.x - (Nf0 - Na0) * inv) + gN1 * (T * r3.y - (Nf1 - Na1) * inv) +
-                                   gN2 * (T * r3.z - (Nf2 - Na2) * inv);
-                            dal += gA * Tend * inv;
-                            T = __fmul_rn(T, __fsub_rn(1.f, al));
-                            const float o = r1.w, hb = r1.z;
-                            float gG = 0.f;
-                            if (pe.alpha_raw < a.alpha_max) {
-                                g[5] = dal * pe.G;
-                                gG = dal * o;
-                            }
-                            float dGdQ = 0.f, dGdb = 0.f;
-                            if (pe.Q > 0.f) {
-                                dGdQ = -0.5f * hb * __fdividef(pe.p, pe.Q) * pe.G;
-                                dGdb = -0.25f * pe.p * (lg2_approx(pe.Q) * ln2) * pe.G;
-                            }
-                            // Q = d^T C d with C = Sigma'^-1 and d = pixel - mean; with m = C d:
-                            // dQ/dmean = -2 m and dQ/dSigma' = -m m^T (accumulated directly:
-                            // going through the conic gradient would cancel for thin splats)
-                            const float gQ = gG * dGdQ;
-                            const float mx = fmaf(r0.z, dx, 0.5f * r0.w * dy), my = fmaf(0.5f * r0.w, dx, r1.x * dy);
-                            g[0] = -2.f * gQ * mx;
-                            g[1] = -2.f * gQ * my;
-                            g[2] = -gQ * mx * mx;
-                            g[3] = -gQ * mx * my;
-                            g[4] = -gQ * my * my;
-                            g[6] = gG * dGdb;
-                            g[7] = gD * w;
-                            g[8] = gC0 * w;
-                            g[9] = gC1 * w;
-                            g[10] = gC2 * w;
-                            g[12] = gN0 * w;
-                            g[13] = gN1 * w;
-                            g[14] = gN2 * w;
+                for (int q = 0; q < 16; ++q) g[q] = 0.f;
+                bool contrib = false;
+                if (c0 + (uint32_t)bit < lp) {
+                    const float4 r0 = slot[bit][0], r1 = slot[bit][1];
+                    const float dx = fpx - r0.x, dy = fpy - r0.y;
+                    PairEval pe;
+                    if (eval_pair(dx, dy, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, a.alpha_max, a.alpha_min, pe)) {
+                        contrib = true;
+                        const float4 r2 = slot[bit][2], r3 = slot[bit][3];
+                        const float al = pe.alpha;
+                        const float w = __fmul_rn(al, T);
+                        Ca0 = __fmaf_rn(w, r2.x, Ca0);
+                        Ca1 = __fmaf_rn(w, r2.y, Ca1);
+                        Ca2 = __fmaf_rn(w, r2.z, Ca2);
+                        Da = __fmaf_rn(w, r2.w, Da);
+                        Na0 = __fmaf_rn(w, r3.x, Na0);
+                        Na1 = __fmaf_rn(w, r3.y, Na1);
+                        Na2 = __fmaf_rn(w, r3.z, Na2);
+                        const float inv = 1.f / (1.f - al);
+                        float dal = gC0 * (T * r2.x - (Cf0 - Ca0) * inv) + gC1 * (T * r2.y - (Cf1 - Ca1) * inv) +
+                                    gC2 * (T * r2.z - (Cf2 - Ca2) * inv);
+                        dal += gD * (T * r2.w - (Df - Da) * inv);
+                        dal += gN0 * (T * r3.x - (Nf0 - Na0) * inv) + gN1 * (T * r3.y - (Nf1 - Na1) * inv) +
+                               gN2 * (T * r3.z - (Nf2 - Na2) * inv);
+                        dal += gA * Tend * inv;
+                        T = __fmul_rn(T, __fsub_rn(1.f, al));
+                        const float o = r1.w, hb = r1.z;
+                        float gG = 0.f;
+                        if (pe.alpha_raw < a.alpha_max) {
+                            g[5] = dal * pe.G;
+                            gG = dal * o;
                         }
-                    }
-                    if (__any_sync(0xffffffffu, contrib)) {
-                        const float sum = warp_reduce16(g, lane);
-                        if ((lane & 1) == 0) atomicAdd(a.g2d + 16 * (size_t)s_ent[j] + (lane >> 1), sum);
+                        float dGdQ = 0.f, dGdb = 0.f;
+                        if (pe.Q > 0.f) {
+                            dGdQ = -0.5f * hb * __fdividef(pe.p, pe.Q) * pe.G;
+                            dGdb = -0.25f * pe.p * (lg2_approx(pe.Q) * ln2) * pe.G;
+                        }
+                        // Q = d^T C d with C = Sigma'^-1 and d = pixel - mean; with m = C d:
+                        // dQ/dmean = -2 m and dQ/dSigma' = -m m^T (accumulated directly:
+                        // going through the conic gradient would cancel for thin splats)
+                        const float gQ = gG * dGdQ;
+                        const float mx = fmaf(r0.z, dx, 0.5f * r0.w * dy), my = fmaf(0.5f * r0.w, dx, r1.x * dy);
+                        g[0] = -2.f * gQ * mx;
+                        g[1] = -2.f * gQ * my;
+                        g[2] = -gQ * mx * mx;
+                        g[3] = -gQ * mx * my;
+                        g[4] = -gQ * my * my;
+                        g[6] = gG * dGdb;
+                        g[7] = gD * w;
+                        g[8] = gC0 * w;
+                        g[9] = gC1 * w;
+                        g[10] = gC2 * w;
+                        g[12] = gN0 * w;
+                        g[13] = gN1 * w;
+                        g[14] = gN2 * w;
                     }
                 }
+                if (__any_sync(0xffffffffu, contrib)) {
+                    const float sum = warp_reduce16(g, lane);
+                    if ((lane & 1) == 0) atomicAdd(a.g2d + 16 * (size_t)went[bit] + (lane >> 1), sum);
+                }
             }
+            __syncwarp();
         }
     }
 }
 
-static size_t fwd_smem(int batch) { return (size_t)batch * (64 + 4 * kCullFields); }
-static size_t bwd_smem(int batch) { return (size_t)batch * (64 + 4 * kCullFields + 4); }
-
 template <int TW, int TH>
 static cudaError_t launch_fwd_t(const FwdArgs &a, int grid, cudaStream_t s) {
-    const size_t smem = fwd_smem(a.batch);
-    k_render_fwd<TW, TH><<<grid, TW * TH, smem, s>>>(a);
+    k_render_fwd<TW, TH><<<grid, TW * TH, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int TW, int TH>
 static cudaError_t launch_bwd_t(const BwdArgs &a, int grid, cudaStream_t s) {
-    const size_t smem = bwd_smem(a.batch);
-    k_render_bwd<TW, TH><<<grid, TW * TH, smem, s>>>(a);
+    k_render_bwd<TW, TH><<<grid, TW * TH, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -382,9 +381,9 @@ static int persistent_grid(bool bwd, int batch) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (bwd)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_bwd<TW, TH>, TW * TH, bwd_smem(batch));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_bwd<TW, TH>, TW * TH, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_fwd<TW, TH>, TW * TH, fwd_smem(batch));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_fwd<TW, TH>, TW * TH, 0);
     if (per < 1) per = 1;
     return sms * per;
 }
