@@ -234,6 +234,7 @@ ges_status ges_bin(int32_t n, int32_t n_views, const ges_camera *cams, const ges
         a.ival[i] = at<uint32_t>(bins, L.ival[i]);
     }
     a.rcount = at<uint32_t>(bins, L.rcount);
+    a.rinfo = at<uint4>(bins, L.rinfo);
     a.ranges = at<uint2>(bins, L.ranges);
     a.queue = at<uint32_t>(bins, L.queue);
     a.hist = at<uint32_t>(bins, L.hist);

@@ -157,18 +157,25 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *key
 
 // Stable scatter: each warp ranks a contiguous 512-key chunk in rounds of 32 with
 // match.any, keeping a per-warp running count per digit; warps are then ordered by
-// an exclusive prefix per digit and CTAs by the scanned digit-major histogram.
+// an exclusive prefix per digit. The CTA's 4096 pairs are first reordered by digit
+// in shared memory, then written out in digit runs (coalesced) at the offsets of
+// the scanned digit-major histogram.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *keys_in, const uint32_t *vals_in,
                                                                uint32_t *keys_out, uint32_t *vals_out,
                                                                const uint32_t *n_dev, uint32_t n_host, int shift,
                                                                uint32_t nblocks, const uint32_t *hist_scanned) {
-    __shared__ uint32_t s_cnt[kSortThreads / 32][256];
+    constexpr int NW = kSortThreads / 32;
+    __shared__ uint32_t s_cnt[NW][256];
+    __shared__ uint32_t s_dstart[256], s_gstart[256];
+    __shared__ uint32_t s_warp[33];
+    __shared__ uint32_t s_keys[kSortTile], s_vals[kSortTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = threadIdx.x; k < (kSortThreads / 32) * 256; k += kSortThreads) (&s_cnt[0][0])[k] = 0u;
+    for (int k = threadIdx.x; k < NW * 256; k += kSortThreads) (&s_cnt[0][0])[k] = 0u;
     __syncthreads();
     const uint32_t n = live_count(n_dev, n_host);
     const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
     if (base >= n) return;  // uniform for the CTA
+    const uint32_t nvalid = (uint32_t)min((uint64_t)kSortTile, (uint64_t)n - base);
     const uint64_t wbase = base + (uint64_t)warp * (kSortItems * 32);
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
@@ -189,10 +196,19 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
     }
     __syncthreads();
     {
+        // digit d = thread: block count, block-local start (exclusive scan over digits),
+        // per-warp offsets inside the digit, and the digit's global start for this CTA
         const int d = threadIdx.x;
-        uint32_t run = hist_scanned[(uint64_t)d * nblocks + blockIdx.x];
+        uint32_t c = 0;
 #pragma unroll
-        for (int w = 0; w < kSortThreads / 32; ++w) {
+        for (int w = 0; w < NW; ++w) c += s_cnt[w][d];
+        uint32_t tot;
+        const uint32_t start = block_excl_scan(c, s_warp, tot);
+        s_dstart[d] = start;
+        s_gstart[d] = hist_scanned[(uint64_t)d * nblocks + blockIdx.x];
+        uint32_t run = start;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
             const uint32_t t = s_cnt[w][d];
             s_cnt[w][d] = run;
             run += t;
@@ -203,9 +219,17 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
     for (int r = 0; r < kSortItems; ++r) {
         if (rank[r] == 0xffffffffu) continue;
         const uint32_t d = (key[r] >> shift) & 0xffu;
-        const uint32_t pos = s_cnt[warp][d] + rank[r];
-        if (keys_out) keys_out[pos] = key[r];
-        vals_out[pos] = val[r];
+        const uint32_t lpos = s_cnt[warp][d] + rank[r];
+        s_keys[lpos] = key[r];
+        s_vals[lpos] = val[r];
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nvalid; i += kSortThreads) {
+        const uint32_t k = s_keys[i];
+        const uint32_t d = (k >> shift) & 0xffu;
+        const uint32_t pos = s_gstart[d] + (i - s_dstart[d]);
+        if (keys_out) keys_out[pos] = k;
+        vals_out[pos] = s_vals[i];
     }
 }
 
@@ -231,34 +255,44 @@ cudaError_t radix_sort(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, con
 
 // ------------------------------------------------------------------ emission
 
+// Depth order -> tiles touched per rank (scanned next into emission offsets), and a
+// rank-ordered copy of what emission needs, so that k_emit streams instead of
+// gathering the binning records a second time.
 __global__ void __launch_bounds__(128) k_gather_counts(const uint32_t *sorted_e, const uint4 *binrec,
-                                                      uint32_t *counts, uint32_t n_entries) {
+                                                      uint32_t *counts, uint4 *rinfo, uint32_t n_entries) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n_entries) counts[r] = binrec[2 * (size_t)sorted_e[r]].z;
+    if (r >= n_entries) return;
+    const uint32_t e = sorted_e[r];
+    const uint32_t tiles = binrec[2 * (size_t)e].z;
+    counts[r] = tiles;
+    if (tiles) {
+        const uint4 bx = binrec[2 * (size_t)e + 1];
+        rinfo[r] = make_uint4(e, bx.x, bx.y, bx.z);
+    }
 }
 
 __global__ void __launch_bounds__(128) k_emit(EmitArgs a) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.n_entries) return;
-    const uint32_t e = a.sorted_e[r];
-    const uint4 br = a.binrec[2 * (size_t)e];
-    const uint32_t tiles = br.z;
-    if (tiles == 0) return;
+    uint64_t off = a.offsets[r];
+    const uint64_t next = (r + 1 < a.n_entries) ? (uint64_t)a.offsets[r + 1] : (uint64_t)*a.total;
+    if (next <= off) return;  // no tiles
+    const uint32_t tiles = (uint32_t)(next - off);
     if (*a.total >= 0xffffffffull) {  // uint32 offsets would wrap
         if (r == 0) set_error(a.err, kErrCapacity);
         return;
     }
-    uint64_t off = a.offsets[r];
     if (off + tiles > a.cap) set_error(a.err, kErrCapacity);
     if (off >= a.cap) return;
-    const uint4 bx = a.binrec[2 * (size_t)e + 1];
+    const uint4 info = a.rinfo[r];
+    const uint32_t e = info.x;
     const int v = (int)(e / (uint32_t)a.n);
     const uint32_t tbase = (uint32_t)a.V.tile_base[v];
     const int tiles_x = a.V.tiles_x[v];
-    const int tx0 = (int)(bx.y & 0xffffu), ty0 = (int)(bx.y >> 16);
-    const int rw = (int)(bx.z & 0xffffu), rh = (int)(bx.z >> 16);
+    const int tx0 = (int)(info.z & 0xffffu), ty0 = (int)(info.z >> 16);
+    const int rw = (int)(info.w & 0xffffu), rh = (int)(info.w >> 16);
     if (rw * rh <= 32) {  // the preprocess kept the hits as a row-major bit mask over the tile box
-        uint32_t m = bx.x;
+        uint32_t m = info.y;
         while (m) {
             const int bit = __ffs(m) - 1;
             m &= m - 1;
@@ -270,6 +304,7 @@ __global__ void __launch_bounds__(128) k_emit(EmitArgs a) {
         }
         return;
     }
+    const uint4 br = a.binrec[2 * (size_t)e];
     const float4 r0 = a.rec[4 * (size_t)e], r1 = a.rec[4 * (size_t)e + 1];
     const float u = r0.x, vv = r0.y, ca = r0.z, cb = r0.w, cc = r1.x;
     const float qm = __fmul_rn(r1.y, kSupportMargin);
@@ -364,13 +399,13 @@ cudaError_t launch_bin(const BinArgs &a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const uint32_t *sorted_e = dv[0];  // 4 passes: result back in buffer 0
     // 2. tiles touched in depth order -> exclusive scan -> emission offsets
-    k_gather_counts<<<ceil_div_u64(nE, 128), 128, 0, s>>>(sorted_e, a.binrec, a.rcount, nE);
+    k_gather_counts<<<ceil_div_u64(nE, 128), 128, 0, s>>>(sorted_e, a.binrec, a.rcount, a.rinfo, nE);
     e = exclusive_scan(a.rcount, a.rcount, nE, a.partials, nullptr, s);
     if (e != cudaSuccess) return e;
     k_set_count<<<1, 1, 0, s>>>(a.total, a.cap, a.header);
     // 3. emit (tile, entry) instances in depth order
     EmitArgs ea;
-    ea.n_entries = nE; ea.n = a.n; ea.sorted_e = sorted_e; ea.offsets = a.rcount; ea.rec = a.rec;
+    ea.n_entries = nE; ea.n = a.n; ea.rinfo = a.rinfo; ea.offsets = a.rcount; ea.rec = a.rec;
     ea.binrec = a.binrec; ea.total = a.total; ea.ikey = a.ikey[0]; ea.ival = a.ival[0]; ea.cap = a.cap;
     ea.err = a.err; ea.V = a.V;
     k_emit<<<ceil_div_u64(nE, 128), 128, 0, s>>>(ea);

@@ -72,11 +72,11 @@ constexpr int kScanMaxPartials = 1024 * 16;
 
 inline uint32_t ceil_div_u64(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
 
-// bins: [header 256][dkey 2 x nV][dval 2 x nV][rank counts nV][ikey 2 x cap][ival 2 x cap]
-//       [ranges T x 8][queue T][hist 256 x nblk][partials]
+// bins: [header 256][dkey 2 x nV][dval 2 x nV][rank counts nV][rank info nV x 16][ikey 2 x cap]
+//       [ival 2 x cap][ranges T x 8][queue T][hist 256 x nblk][partials]
 // header: u32 n_inst (instances actually listed) at 0, u32 queue counters at 4 and 8.
 struct BinsLayout {
-    uint64_t dkey[2], dval[2], rcount, ikey[2], ival[2], ranges, queue, hist, partials, bytes;
+    uint64_t dkey[2], dval[2], rcount, rinfo, ikey[2], ival[2], ranges, queue, hist, partials, bytes;
     uint32_t n_tiles;
     uint32_t nblk_entries, nblk_inst;  // radix CTAs for the depth sort and the tile sort
     int tile_passes;                   // 8-bit passes of the tile sort
@@ -96,6 +96,7 @@ inline BinsLayout bins_layout(int32_t n, int32_t n_views, uint32_t n_tiles, uint
     for (int i = 0; i < 2; ++i) { L.dkey[i] = off; off = align256(off + nv * 4); }
     for (int i = 0; i < 2; ++i) { L.dval[i] = off; off = align256(off + nv * 4); }
     L.rcount = off; off = align256(off + nv * 4 + 4);
+    L.rinfo = off; off = align256(off + nv * 16);
     for (int i = 0; i < 2; ++i) { L.ikey[i] = off; off = align256(off + cap * 4); }
     for (int i = 0; i < 2; ++i) { L.ival[i] = off; off = align256(off + cap * 4); }
     L.ranges = off; off = align256(off + (uint64_t)n_tiles * 8);
@@ -316,7 +317,7 @@ struct PreBwdArgs {
 struct EmitArgs {
     uint32_t n_entries;
     int n;  // splats per view
-    const uint32_t *sorted_e;  // entries in depth order
+    const uint4 *rinfo;        // per rank: entry, hit mask, tile box origin, tile box size
     const uint32_t *offsets;   // exclusive scan of tiles touched in that order
     const float4 *rec;
     const uint4 *binrec;
@@ -337,6 +338,7 @@ struct BinArgs {
     // bins
     uint32_t *header;  // [0] n_inst
     uint32_t *dkey[2], *dval[2], *rcount, *ikey[2], *ival[2];
+    uint4 *rinfo;
     uint2 *ranges;
     uint32_t *queue;
     uint32_t *hist, *partials;
