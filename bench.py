@@ -51,6 +51,8 @@ def parse_args():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the oracle sample")
+    p.add_argument("--splats", type=int, default=None,
+                   help="override the workload's splat count (smaller cases for profiling; not a bench line)")
     return p.parse_args()
 
 
@@ -135,7 +137,7 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- workload
-def make_workload(name: str, rank: int = 0):
+def make_workload(name: str, rank: int = 0, n_override=None):
     from paper_2411_09156_gb300.drt import drt_sizes
     from paper_2411_09156_gb300.scenes import random_sphere_cameras, workload
     if name == "drt8-1.5M":
@@ -144,7 +146,7 @@ def make_workload(name: str, rank: int = 0):
         sizes = drt_sizes(1920, 1080, 16)
     else:
         sizes = None
-    sc, cams = workload(name, sizes=sizes)
+    sc, cams = workload(name, sizes=sizes, n_override=n_override)
     if rank > 0 and sizes is not None:  # independent batch of views per rank
         cams = random_sphere_cameras(np.random.default_rng(1000 + rank), len(sizes), 5.0, sizes)
     return sc, cams
@@ -217,7 +219,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     from paper_2411_09156_gb300.api import GESConfig
-    sc, cams = make_workload(args.workload)
+    sc, cams = make_workload(args.workload, 0, args.splats)
     cfg = GESConfig(sh_degree=sc.sh_degree, persistent=1)
     from oracle import oracle as O
     O.build_oracle()
@@ -254,7 +256,7 @@ def main():
 
     torch.cuda.set_device(local)
     dev_name = torch.cuda.get_device_name()
-    sc, cams = make_workload(args.workload, rank)
+    sc, cams = make_workload(args.workload, rank, args.splats)
     inputs = api.scene_tensors(sc)
     P = sum(c.width * c.height for c in cams)
     ups = upstream_grads(P, 1000 + rank)
@@ -416,7 +418,8 @@ def main():
             "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded heightfield scene, random upstream grads)",
-            "config": {"workload": args.workload, "splats": sc.n, "views": len(cams),
+            "config": {"workload": args.workload if args.splats is None else f"{args.workload} (splats={sc.n})",
+                       "splats": sc.n, "views": len(cams),
                        "sizes": [[c.width, c.height] for c in cams], "pixels": P, "sh_degree": sc.sh_degree,
                        "tile": [cfg.tile_w, cfg.tile_h], "batch": cfg.batch, "persistent": cfg.persistent,
                        "instances": n_inst, "l2": "flushed between steps (256 MB write)", "gpu": dev_name,

@@ -267,6 +267,27 @@ __device__ __forceinline__ void sh_grad(int deg, float x, float y, float z, floa
     dY[15][0] = -3.f * kSH3a * (xx - yy); dY[15][1] = 6.f * kSH3a * x * y; dY[15][2] = 0.f;
 }
 
+// Gradient of sum_k al[k] Y_k with respect to (x, y, z), accumulated into g
+// without forming the per-basis gradients (same polynomials as sh_grad).
+__device__ __forceinline__ void sh_grad_dot(int deg, float x, float y, float z, const float *al, float &gx,
+                                            float &gy, float &gz) {
+    gx = 0.f; gy = 0.f; gz = 0.f;
+    if (deg < 1) return;
+    gy -= kSH1 * al[1]; gz += kSH1 * al[2]; gx -= kSH1 * al[3];
+    if (deg < 2) return;
+    gx += kSH2a * (y * al[4] - z * al[7]) + 2.f * kSH2c * x * al[8];
+    gy += kSH2a * (x * al[4] - z * al[5]) - 2.f * kSH2c * y * al[8];
+    gz += -kSH2a * (y * al[5] + x * al[7]) + 6.f * kSH2b * z * al[6];
+    if (deg < 3) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gx += -6.f * kSH3a * x * y * al[9] + kSH3b * y * z * al[10] - kSH3c * (5.f * zz - 1.f) * al[13] +
+          2.f * kSH3e * x * z * al[14] - 3.f * kSH3a * (xx - yy) * al[15];
+    gy += -3.f * kSH3a * (xx - yy) * al[9] + kSH3b * x * z * al[10] - kSH3c * (5.f * zz - 1.f) * al[11] -
+          2.f * kSH3e * y * z * al[14] + 6.f * kSH3a * x * y * al[15];
+    gz += kSH3b * x * y * al[10] - 10.f * kSH3c * y * z * al[11] + kSH3d * (15.f * zz - 3.f) * al[12] -
+          10.f * kSH3c * x * z * al[13] + kSH3e * (xx - yy) * al[14];
+}
+
 // phi(beta) of Eq. 7 by reading mode, and d phi / d beta.
 __device__ __forceinline__ float phi_beta(float beta, float rho, int mode, float &dphi) {
     if (mode == 0) { dphi = 0.f; return 1.f; }

@@ -206,15 +206,37 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
 // summed over views in registers and written once (overwrite).
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const float4 po = a.pos_op[i];
-    const float4 ls = a.lsb[i];
-    const float4 q4 = a.quat[i];
+// Sum over the `width` lanes of a segment (width a power of two <= 32); every lane
+// of the segment receives the sum.
+__device__ __forceinline__ float seg_sum(float x, int width) {
+    for (int o = width >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// One lane per (splat, view): the lanes of a splat are adjacent (a segment of
+// `seg` lanes, the view count rounded up to a power of two), each lane takes its
+// view's screen-space gradient back through S1-S4, and the per-splat sums over
+// views are formed with shuffles inside the segment. Lane 0 of the segment
+// writes the geometry gradients; the SH coefficient gradients are written by all
+// lanes of the segment, coefficient k by lane k mod seg.
+__global__ void __launch_bounds__(256) k_preprocess_bwd(PreBwdArgs a) {
+    const int NV = a.V.n_views;
+    int seg = 1;
+    while (seg < NV) seg <<= 1;
+    const int lane = threadIdx.x & 31;
+    const int spw = 32 / seg;  // splats per warp
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int v = lane % seg;
+    const long long il = gw * spw + lane / seg;
+    if (gw * spw >= a.n) return;  // whole warp past the end (warp-uniform)
+    const bool splat_ok = il < a.n;
+    const int i = splat_ok ? (int)il : a.n - 1;
+    const bool active = splat_ok && v < NV;
+    const float4 po = __ldg(a.pos_op + i);
+    const float4 ls = __ldg(a.lsb + i);
+    const float4 q4 = __ldg(a.quat + i);
     const float beta = ls.w;
-    const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
-    const float qinv = rsqrtf(qn2);
+    const float qinv = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
     const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
     float R[9];
     quat_rot(qw, qx, qy, qz, R);
@@ -228,21 +250,22 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
     if (ls.y < ls.x) ks = 1;
     if (ls.z < (ks == 0 ? ls.x : ls.y)) ks = 2;
     const int K = a.P.n_coeffs;
-    // accumulators over views
-    float gmu[3] = {0.f, 0.f, 0.f}, gop = 0.f, gl[3] = {0.f, 0.f, 0.f}, gbeta = 0.f;
+    // this lane's view
+    float gmu[3] = {0.f, 0.f, 0.f}, gop = 0.f, gbeta = 0.f;
     float GR[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float gD[3] = {0.f, 0.f, 0.f};  // dL/d(s'_k^2)
-    float gsh[16][3];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) { gsh[k][0] = 0.f; gsh[k][1] = 0.f; gsh[k][2] = 0.f; }
-
-    for (int v = 0; v < a.V.n_views; ++v) {
+    float wc[3] = {0.f, 0.f, 0.f};  // colour gradient where the channel was not clamped
+    float sdir[3] = {0.f, 0.f, 0.f};
+    bool has = false;
+    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0, g3 = g0;
+    if (active) {
         const size_t e = (size_t)v * a.n + i;
-        const float4 g0 = a.g2d[4 * e + 0], g1 = a.g2d[4 * e + 1], g2 = a.g2d[4 * e + 2], g3 = a.g2d[4 * e + 3];
-        if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && g1.x == 0.f && g1.y == 0.f &&
-            g1.z == 0.f && g1.w == 0.f && g2.x == 0.f && g2.y == 0.f && g2.z == 0.f && g3.x == 0.f &&
-            g3.y == 0.f && g3.z == 0.f)
-            continue;
+        g0 = a.g2d[4 * e + 0]; g1 = a.g2d[4 * e + 1]; g2 = a.g2d[4 * e + 2]; g3 = a.g2d[4 * e + 3];
+        has = !(g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && g1.x == 0.f && g1.y == 0.f &&
+                g1.z == 0.f && g1.w == 0.f && g2.x == 0.f && g2.y == 0.f && g2.z == 0.f && g3.x == 0.f &&
+                g3.y == 0.f && g3.z == 0.f);
+    }
+    if (has) {
         const float *vm = a.V.vm[v];
         const float tx = vm[0] * po.x + vm[1] * po.y + vm[2] * po.z + vm[3];
         const float ty = vm[4] * po.x + vm[5] * po.y + vm[6] * po.z + vm[7];
@@ -262,19 +285,17 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
         // Sigma' = sum_k s'_k^2 u_k u_k^T + h I with u_k = T r_k. With w_k = G_M u_k:
         //   dL/d(s'_k^2) += u_k . w_k,  dL/dR[:, k] += 2 s'_k^2 T^T w_k,
         //   dL/dT = 2 sum_k s'_k^2 w_k r_k^T
-        // (equal to G_Sigma = T^T G_M T, G_R = 2 G_Sigma R D, G_T = 2 G_M T Sigma, but
-        // without the cancellation of forming G_Sigma for a nearly flat splat)
         float GT[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float ux = T[0] * R[k] + T[1] * R[3 + k] + T[2] * R[6 + k];
             const float uy = T[3] * R[k] + T[4] * R[3 + k] + T[5] * R[6 + k];
             const float wx = M00 * ux + M01 * uy, wy = M01 * ux + M11 * uy;
-            gD[k] += ux * wx + uy * wy;
+            gD[k] = ux * wx + uy * wy;
             const float s2 = 2.f * dd[k];
-            GR[0 + k] += s2 * (T[0] * wx + T[3] * wy);
-            GR[3 + k] += s2 * (T[1] * wx + T[4] * wy);
-            GR[6 + k] += s2 * (T[2] * wx + T[5] * wy);
+            GR[0 + k] = s2 * (T[0] * wx + T[3] * wy);
+            GR[3 + k] = s2 * (T[1] * wx + T[4] * wy);
+            GR[6 + k] = s2 * (T[2] * wx + T[5] * wy);
             GT[0] += s2 * wx * R[k]; GT[1] += s2 * wx * R[3 + k]; GT[2] += s2 * wx * R[6 + k];
             GT[3] += s2 * wy * R[k]; GT[4] += s2 * wy * R[3 + k]; GT[5] += s2 * wy * R[6 + k];
         }
@@ -294,11 +315,11 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
         gt0 += fx * iz * g0.x; gt2 += -fx * tx * iz2 * g0.x;
         gt1 += fy * iz * g0.y; gt2 += -fy * ty * iz2 * g0.y;
         gt2 += g1.w;
-        gmu[0] += vm[0] * gt0 + vm[4] * gt1 + vm[8] * gt2;
-        gmu[1] += vm[1] * gt0 + vm[5] * gt1 + vm[9] * gt2;
-        gmu[2] += vm[2] * gt0 + vm[6] * gt1 + vm[10] * gt2;
-        gop += g1.y;
-        gbeta += g1.z;
+        gmu[0] = vm[0] * gt0 + vm[4] * gt1 + vm[8] * gt2;
+        gmu[1] = vm[1] * gt0 + vm[5] * gt1 + vm[9] * gt2;
+        gmu[2] = vm[2] * gt0 + vm[6] * gt1 + vm[10] * gt2;
+        gop = g1.y;
+        gbeta = g1.z;
         // normal: n = sign R[:, ks]
         const float f = R[0 + ks] * (a.V.campos[v][0] - po.x) + R[3 + ks] * (a.V.campos[v][1] - po.y) +
                         R[6 + ks] * (a.V.campos[v][2] - po.z);
@@ -311,59 +332,81 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(PreBwdArgs a) {
             float dx = po.x - a.V.campos[v][0], dy = po.y - a.V.campos[v][1], dz = po.z - a.V.campos[v][2];
             const float dinv = rsqrtf(dx * dx + dy * dy + dz * dz);
             dx *= dinv; dy *= dinv; dz *= dinv;
-            float Y[16], dY[16][3];
+            sdir[0] = dx; sdir[1] = dy; sdir[2] = dz;
+            float Y[16];
             sh_eval(a.P.sh_degree, dx, dy, dz, Y);
-            sh_grad(a.P.sh_degree, dx, dy, dz, dY);
             const float *cf = a.color + (size_t)i * K * 3;
             const float gc[3] = {g2.x, g2.y, g2.z};
-            float gd0 = 0.f, gd1 = 0.f, gd2 = 0.f;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 float pre = 0.5f;
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
                     if (k < K) pre = fmaf(__ldg(cf + 3 * k + ch), Y[k], pre);
-                if (!(pre > 0.f)) continue;
-#pragma unroll
-                for (int k = 0; k < 16; ++k)
-                    if (k < K) {
-                        gsh[k][ch] += gc[ch] * Y[k];
-                        const float w = gc[ch] * __ldg(cf + 3 * k + ch);
-                        gd0 += w * dY[k][0]; gd1 += w * dY[k][1]; gd2 += w * dY[k][2];
-                    }
+                if (pre > 0.f) wc[ch] = gc[ch];
             }
+            // d/dd of sum_c wc_c sum_k c_kc Y_k(d): one polynomial with coefficients al_k
+            float al[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                al[k] = (k < K) ? wc[0] * __ldg(cf + 3 * k) + wc[1] * __ldg(cf + 3 * k + 1) + wc[2] * __ldg(cf + 3 * k + 2)
+                                : 0.f;
+            float gd0, gd1, gd2;
+            sh_grad_dot(a.P.sh_degree, dx, dy, dz, al, gd0, gd1, gd2);
             const float dot = gd0 * dx + gd1 * dy + gd2 * dz;
             gmu[0] += (gd0 - dx * dot) * dinv;
             gmu[1] += (gd1 - dy * dot) * dinv;
             gmu[2] += (gd2 - dz * dot) * dinv;
         } else {
-            gsh[0][0] += g2.x; gsh[0][1] += g2.y; gsh[0][2] += g2.z;
+            wc[0] = g2.x; wc[1] = g2.y; wc[2] = g2.z;
         }
     }
-    // s'_k = phi(beta) exp(l_k): dL/dl_k = 2 s'_k^2 gD_k, dL/dbeta += 2 s'_k gD_k phi'(beta) exp(l_k)
+    // sums over the views of this splat
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float gsp = 2.f * sp[k] * gD[k];
-        gl[k] = gsp * sp[k];
-        gbeta += gsp * dphi * es[k];
+    for (int k = 0; k < 3; ++k) { gmu[k] = seg_sum(gmu[k], seg); gD[k] = seg_sum(gD[k], seg); }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) GR[k] = seg_sum(GR[k], seg);
+    gop = seg_sum(gop, seg);
+    gbeta = seg_sum(gbeta, seg);
+    if (splat_ok && v == 0) {
+        // s'_k = phi(beta) exp(l_k): dL/dl_k = 2 s'_k^2 gD_k, dL/dbeta += 2 s'_k gD_k phi'(beta) exp(l_k)
+        float gl[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float gsp = 2.f * sp[k] * gD[k];
+            gl[k] = gsp * sp[k];
+            gbeta += gsp * dphi * es[k];
+        }
+        // R(q) -> unit quaternion -> quaternion
+        const float w = qw, x = qx, y = qy, z = qz;
+        const float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+        const float gx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] + w * GR[7] - 2.f * x * GR[8]);
+        const float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6] + z * GR[7] - 2.f * y * GR[8]);
+        const float gz = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] + y * GR[5] + x * GR[6] + y * GR[7]);
+        const float dq = gw * w + gx * x + gy * y + gz * z;
+        a.g_quat[i] = make_float4((gw - w * dq) * qinv, (gx - x * dq) * qinv, (gy - y * dq) * qinv, (gz - z * dq) * qinv);
+        a.g_pos_op[i] = make_float4(gmu[0], gmu[1], gmu[2], gop);
+        a.g_lsb[i] = make_float4(gl[0], gl[1], gl[2], gbeta);
     }
-    // R(q) -> unit quaternion -> quaternion
-    const float w = qw, x = qx, y = qy, z = qz;
-    const float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
-    const float gx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] + w * GR[7] - 2.f * x * GR[8]);
-    const float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6] + z * GR[7] - 2.f * y * GR[8]);
-    const float gz = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] + y * GR[5] + x * GR[6] + y * GR[7]);
-    const float dq = gw * w + gx * x + gy * y + gz * z;
-    a.g_quat[i] = make_float4((gw - w * dq) * qinv, (gx - x * dq) * qinv, (gy - y * dq) * qinv, (gz - z * dq) * qinv);
-    a.g_pos_op[i] = make_float4(gmu[0], gmu[1], gmu[2], gop);
-    a.g_lsb[i] = make_float4(gl[0], gl[1], gl[2], gbeta);
-    if (a.P.sh_degree >= 0) {
-        float *gcol = a.g_color + (size_t)i * K * 3;
+    // colour coefficients: dL/dc_kc = sum_v wc_vc Y_k(d_v) (RGB mode: sum_v wc_vc)
+    if (a.P.sh_degree < 0) {
+        float s0 = seg_sum(wc[0], seg), s1 = seg_sum(wc[1], seg), s2 = seg_sum(wc[2], seg);
+        if (splat_ok && v == 0) { a.g_color[3 * (size_t)i] = s0; a.g_color[3 * (size_t)i + 1] = s1; a.g_color[3 * (size_t)i + 2] = s2; }
+        return;
+    }
+    float Y[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < K) { gcol[3 * k] = gsh[k][0]; gcol[3 * k + 1] = gsh[k][1]; gcol[3 * k + 2] = gsh[k][2]; }
-    } else {
-        a.g_color[3 * i] = gsh[0][0]; a.g_color[3 * i + 1] = gsh[0][1]; a.g_color[3 * i + 2] = gsh[0][2];
+    for (int k = 0; k < 16; ++k) Y[k] = 0.f;
+    if (has) sh_eval(a.P.sh_degree, sdir[0], sdir[1], sdir[2], Y);
+    float *gcol = a.g_color + (size_t)i * K * 3;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (k >= K) break;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float t = seg_sum(wc[ch] * Y[k], seg);
+            if (splat_ok && (k % seg) == v) gcol[3 * k + ch] = t;
+        }
     }
 }
 
@@ -376,7 +419,10 @@ cudaError_t launch_preprocess(const PreArgs &a, cudaStream_t s) {
 
 cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    k_preprocess_bwd<<<(a.n + 127) / 128, 128, 0, s>>>(a);
+    int seg = 1;
+    while (seg < a.V.n_views) seg <<= 1;
+    const long long warps = ((long long)a.n + (32 / seg) - 1) / (32 / seg);
+    k_preprocess_bwd<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
