@@ -43,11 +43,13 @@ __device__ __forceinline__ void load_sh_rgb(const float *color, int K, size_t i,
         }
     } else {
         const float *c = color + i * (size_t)K * 3;
-        for (int k = 0; k < K; ++k) {
-            r = fmaf(__ldg(c + 3 * k), Y[k], r);
-            g = fmaf(__ldg(c + 3 * k + 1), Y[k], g);
-            b = fmaf(__ldg(c + 3 * k + 2), Y[k], b);
-        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < K) {
+                r = fmaf(__ldg(c + 3 * k), Y[k], r);
+                g = fmaf(__ldg(c + 3 * k + 1), Y[k], g);
+                b = fmaf(__ldg(c + 3 * k + 2), Y[k], b);
+            }
     }
     r = fmaxf(r, 0.f); g = fmaxf(g, 0.f); b = fmaxf(b, 0.f);
 }
@@ -166,7 +168,9 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
                 int ks = 0;
                 if (ls.y < ls.x) ks = 1;
                 if (ls.z < (ks == 0 ? ls.x : ls.y)) ks = 2;
-                const float nx = R[0 + ks], ny = R[3 + ks], nz = R[6 + ks];
+                const float nx = ks == 0 ? R[0] : (ks == 1 ? R[1] : R[2]);
+                const float ny = ks == 0 ? R[3] : (ks == 1 ? R[4] : R[5]);
+                const float nz = ks == 0 ? R[6] : (ks == 1 ? R[7] : R[8]);
                 const float f = nx * (a.V.campos[v][0] - po.x) + ny * (a.V.campos[v][1] - po.y) +
                                 nz * (a.V.campos[v][2] - po.z);
                 const float sg = f < 0.f ? -1.f : 1.f;
@@ -213,6 +217,32 @@ __device__ __forceinline__ float seg_sum(float x, int width) {
     return x;
 }
 
+// Recursive-halving sum of 48 values over a segment of SEG lanes (compile-time
+// sizes keep every index static, so the values stay in registers); each lane ends
+// with 48/SEG of the sums and writes the ones that exist (k < K).
+template <int SEG>
+__device__ __forceinline__ void write_sh_grad(float (&t)[48], int v, int K, bool ok, float *gcol) {
+    int base = 0;
+#pragma unroll
+    for (int o = SEG >> 1, cnt = 48; o > 0; o >>= 1, cnt >>= 1) {
+        const int h = cnt >> 1;
+        const bool up = (v & o) != 0;
+#pragma unroll
+        for (int q = 0; q < h; ++q) {
+            const float send = up ? t[q] : t[q + h];
+            const float keep = up ? t[q + h] : t[q];
+            t[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+        if (up) base += h;
+    }
+    constexpr int CNT = 48 / SEG;
+    if (ok) {
+#pragma unroll
+        for (int q = 0; q < CNT; ++q)
+            if (base + q < K * 3) gcol[base + q] = t[q];
+    }
+}
+
 // One lane per (splat, view): the lanes of a splat are adjacent (a segment of
 // `seg` lanes, the view count rounded up to a power of two), each lane takes its
 // view's screen-space gradient back through S1-S4, and the per-splat sums over
@@ -232,6 +262,25 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(PreBwdArgs a) {
     const bool splat_ok = il < a.n;
     const int i = splat_ok ? (int)il : a.n - 1;
     const bool active = splat_ok && v < NV;
+    // the SH coefficients of the warp's splats, loaded once with coalesced float4 reads
+    // (dynamic shared memory: spw * K * 3 floats per warp)
+    extern __shared__ float s_sh[];
+    const int K = a.P.n_coeffs;
+    float *wsh = s_sh + (threadIdx.x >> 5) * (spw * K * 3);
+    if (a.P.sh_degree >= 0) {
+        const long long first = gw * spw;
+        const int nsp = (int)min((long long)spw, (long long)a.n - first);
+        const int nflt = nsp * K * 3;
+        const float *src = a.color + (size_t)first * K * 3;
+        if ((K * 3) % 4 == 0) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(src);
+            for (int q = lane; q < nflt / 4; q += 32) reinterpret_cast<float4 *>(wsh)[q] = __ldg(s4 + q);
+        } else {
+            for (int q = lane; q < nflt; q += 32) wsh[q] = __ldg(src + q);
+        }
+        __syncwarp();
+    }
+    const float *cf = wsh + (lane / seg) * K * 3;  // this lane's splat
     const float4 po = __ldg(a.pos_op + i);
     const float4 ls = __ldg(a.lsb + i);
     const float4 q4 = __ldg(a.quat + i);
@@ -249,7 +298,6 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(PreBwdArgs a) {
     int ks = 0;
     if (ls.y < ls.x) ks = 1;
     if (ls.z < (ks == 0 ? ls.x : ls.y)) ks = 2;
-    const int K = a.P.n_coeffs;
     // this lane's view
     float gmu[3] = {0.f, 0.f, 0.f}, gop = 0.f, gbeta = 0.f;
     float GR[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -320,13 +368,20 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(PreBwdArgs a) {
         gmu[2] = vm[2] * gt0 + vm[6] * gt1 + vm[10] * gt2;
         gop = g1.y;
         gbeta = g1.z;
-        // normal: n = sign R[:, ks]
-        const float f = R[0 + ks] * (a.V.campos[v][0] - po.x) + R[3 + ks] * (a.V.campos[v][1] - po.y) +
-                        R[6 + ks] * (a.V.campos[v][2] - po.z);
+        // normal: n = sign R[:, ks] (column chosen with selects: a runtime index would
+        // move R and GR to local memory)
+        const float nx = ks == 0 ? R[0] : (ks == 1 ? R[1] : R[2]);
+        const float ny = ks == 0 ? R[3] : (ks == 1 ? R[4] : R[5]);
+        const float nz = ks == 0 ? R[6] : (ks == 1 ? R[7] : R[8]);
+        const float f = nx * (a.V.campos[v][0] - po.x) + ny * (a.V.campos[v][1] - po.y) + nz * (a.V.campos[v][2] - po.z);
         const float sg = f < 0.f ? -1.f : 1.f;
-        GR[0 + ks] += sg * g3.x;
-        GR[3 + ks] += sg * g3.y;
-        GR[6 + ks] += sg * g3.z;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float on = (ks == c) ? sg : 0.f;
+            GR[0 + c] += on * g3.x;
+            GR[3 + c] += on * g3.y;
+            GR[6 + c] += on * g3.z;
+        }
         // colour
         if (a.P.sh_degree >= 0) {
             float dx = po.x - a.V.campos[v][0], dy = po.y - a.V.campos[v][1], dz = po.z - a.V.campos[v][2];
@@ -335,22 +390,20 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(PreBwdArgs a) {
             sdir[0] = dx; sdir[1] = dy; sdir[2] = dz;
             float Y[16];
             sh_eval(a.P.sh_degree, dx, dy, dz, Y);
-            const float *cf = a.color + (size_t)i * K * 3;
             const float gc[3] = {g2.x, g2.y, g2.z};
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 float pre = 0.5f;
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
-                    if (k < K) pre = fmaf(__ldg(cf + 3 * k + ch), Y[k], pre);
+                    if (k < K) pre = fmaf(cf[3 * k + ch], Y[k], pre);
                 if (pre > 0.f) wc[ch] = gc[ch];
             }
             // d/dd of sum_c wc_c sum_k c_kc Y_k(d): one polynomial with coefficients al_k
             float al[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k)
-                al[k] = (k < K) ? wc[0] * __ldg(cf + 3 * k) + wc[1] * __ldg(cf + 3 * k + 1) + wc[2] * __ldg(cf + 3 * k + 2)
-                                : 0.f;
+                al[k] = (k < K) ? wc[0] * cf[3 * k] + wc[1] * cf[3 * k + 1] + wc[2] * cf[3 * k + 2] : 0.f;
             float gd0, gd1, gd2;
             sh_grad_dot(a.P.sh_degree, dx, dy, dz, al, gd0, gd1, gd2);
             const float dot = gd0 * dx + gd1 * dy + gd2 * dz;
@@ -398,15 +451,20 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(PreBwdArgs a) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) Y[k] = 0.f;
     if (has) sh_eval(a.P.sh_degree, sdir[0], sdir[1], sdir[2], Y);
+    // the 48 products wc_c Y_k summed over the segment's lanes by recursive halving:
+    // at each level a lane keeps half of its values and adds its partner's copy of
+    // them, so 48 values cost 24 + 12 + ... shuffles instead of 48 per level
+    float t[48];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) { t[3 * k] = wc[0] * Y[k]; t[3 * k + 1] = wc[1] * Y[k]; t[3 * k + 2] = wc[2] * Y[k]; }
     float *gcol = a.g_color + (size_t)i * K * 3;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        if (k >= K) break;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            const float t = seg_sum(wc[ch] * Y[k], seg);
-            if (splat_ok && (k % seg) == v) gcol[3 * k + ch] = t;
-        }
+    switch (seg) {
+        case 1: write_sh_grad<1>(t, v, K, splat_ok, gcol); break;
+        case 2: write_sh_grad<2>(t, v, K, splat_ok, gcol); break;
+        case 4: write_sh_grad<4>(t, v, K, splat_ok, gcol); break;
+        case 8: write_sh_grad<8>(t, v, K, splat_ok, gcol); break;
+        case 16: write_sh_grad<16>(t, v, K, splat_ok, gcol); break;
+        default: write_sh_grad<32>(t, v, K, splat_ok, gcol); break;
     }
 }
 
@@ -422,7 +480,8 @@ cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t s) {
     int seg = 1;
     while (seg < a.V.n_views) seg <<= 1;
     const long long warps = ((long long)a.n + (32 / seg) - 1) / (32 / seg);
-    k_preprocess_bwd<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(a);
+    const size_t smem = a.P.sh_degree >= 0 ? (size_t)8 * (32 / seg) * a.P.n_coeffs * 3 * sizeof(float) : 0;
+    k_preprocess_bwd<<<(unsigned)((warps * 32 + 255) / 256), 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
