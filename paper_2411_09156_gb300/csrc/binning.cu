@@ -141,10 +141,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *key
     const uint32_t n = live_count(n_dev, n_host);
     const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
     if (base < n) {
-#pragma unroll 4
+        uint32_t kk[kSortItems];
+#pragma unroll
         for (int k = 0; k < kSortItems; ++k) {
-            uint64_t idx = base + (uint64_t)k * kSortThreads + threadIdx.x;
-            if (idx < n) atomicAdd(&s_h[warp][(keys[idx] >> shift) & 0xffu], 1u);
+            const uint64_t idx = base + (uint64_t)k * kSortThreads + threadIdx.x;
+            kk[k] = idx < n ? __ldg(keys + idx) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k) {
+            const uint64_t idx = base + (uint64_t)k * kSortThreads + threadIdx.x;
+            if (idx < n) atomicAdd(&s_h[warp][(kk[k] >> shift) & 0xffu], 1u);
         }
     }
     __syncthreads();
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *key
 // an exclusive prefix per digit. The CTA's 4096 pairs are first reordered by digit
 // in shared memory, then written out in digit runs (coalesced) at the offsets of
 // the scanned digit-major histogram.
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *keys_in, const uint32_t *vals_in,
+__global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(const uint32_t *keys_in, const uint32_t *vals_in,
                                                                uint32_t *keys_out, uint32_t *vals_out,
                                                                const uint32_t *n_dev, uint32_t n_host, int shift,
                                                                uint32_t nblocks, const uint32_t *hist_scanned) {
@@ -179,12 +185,18 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
     const uint64_t wbase = base + (uint64_t)warp * (kSortItems * 32);
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+    // all loads first, so that the 16 rounds' reads are in flight together
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
         const bool valid = idx < n;
-        key[r] = valid ? keys_in[idx] : 0u;
-        val[r] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
+        key[r] = valid ? __ldg(keys_in + idx) : 0u;
+        val[r] = valid ? (vals_in ? __ldg(vals_in + idx) : (uint32_t)idx) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
+        const bool valid = idx < n;
         const uint32_t d = (key[r] >> shift) & 0xffu;
         const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
         uint32_t before = 0;
@@ -257,53 +269,111 @@ cudaError_t radix_sort(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, con
 
 // Depth order -> tiles touched per rank (scanned next into emission offsets), and a
 // rank-ordered copy of what emission needs, so that k_emit streams instead of
-// gathering the binning records a second time.
+// gathering the binning records a second time. rinfo per rank: entry, hit mask,
+// global key of the tile box's first tile, and (box width in tiles | view tiles
+// per row << 6); box width 0 marks a box of more than 32 tiles (no mask).
 __global__ void __launch_bounds__(128) k_gather_counts(const uint32_t *sorted_e, const uint4 *binrec,
-                                                      uint32_t *counts, uint4 *rinfo, uint32_t n_entries) {
+                                                      uint32_t *counts, uint4 *rinfo, uint32_t n_entries, int n,
+                                                      ViewSet V) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_entries) return;
-    const uint32_t e = sorted_e[r];
-    const uint32_t tiles = binrec[2 * (size_t)e].z;
+    const uint32_t e = __ldg(sorted_e + r);
+    // both halves of the 32-byte record in one round trip
+    const uint4 b0 = __ldg(binrec + 2 * (size_t)e), b1 = __ldg(binrec + 2 * (size_t)e + 1);
+    const uint32_t tiles = b0.z;
     counts[r] = tiles;
     if (tiles) {
-        const uint4 bx = binrec[2 * (size_t)e + 1];
-        rinfo[r] = make_uint4(e, bx.x, bx.y, bx.z);
+        const int v = (int)(e / (uint32_t)n);
+        const int tx0 = (int)(b1.y & 0xffffu), ty0 = (int)(b1.y >> 16);
+        const int rw = (int)(b1.z & 0xffffu), rh = (int)(b1.z >> 16);
+        const int tiles_x = V.tiles_x[v];
+        const uint32_t origin = (uint32_t)V.tile_base[v] + (uint32_t)(ty0 * tiles_x + tx0);
+        const uint32_t shape = (rw * rh <= 32 ? (uint32_t)rw : 0u) | ((uint32_t)tiles_x << 6);
+        rinfo[r] = make_uint4(e, b1.x, origin, shape);
     }
 }
 
+// Position of the k-th (0-based) set bit of m; m has more than k set bits.
+__device__ __forceinline__ uint32_t select_bit(uint32_t m, uint32_t k) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const uint32_t lo = m & ((1u << s) - 1u);
+        const uint32_t c = (uint32_t)__popc(lo);
+        if (k >= c) { k -= c; m >>= s; pos += s; } else { m = lo; }
+    }
+    return pos;
+}
+
+// Emission. Ranks r..r+31 of a warp own the contiguous instance range
+// [offsets[r], offsets[r+32]); the warp expands their hit masks together, 32
+// instances per round: instance j goes to the rank whose prefix interval holds j
+// (binary search over the warp's inclusive prefix) and to that rank's j-th set
+// mask bit. Writes are coalesced. Boxes of more than 32 tiles (no mask) are
+// expanded afterwards by their own lane with the tile test.
 __global__ void __launch_bounds__(128) k_emit(EmitArgs a) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= a.n_entries) return;
-    uint64_t off = a.offsets[r];
-    const uint64_t next = (r + 1 < a.n_entries) ? (uint64_t)a.offsets[r + 1] : (uint64_t)*a.total;
-    if (next <= off) return;  // no tiles
-    const uint32_t tiles = (uint32_t)(next - off);
-    if (*a.total >= 0xffffffffull) {  // uint32 offsets would wrap
+    const int lane = threadIdx.x & 31;
+    const unsigned long long total = *a.total;
+    if (total >= 0xffffffffull) {  // uint32 offsets would wrap
         if (r == 0) set_error(a.err, kErrCapacity);
         return;
     }
-    if (off + tiles > a.cap) set_error(a.err, kErrCapacity);
-    if (off >= a.cap) return;
-    const uint4 info = a.rinfo[r];
+    if (blockIdx.x * blockDim.x + (threadIdx.x & ~31u) >= a.n_entries) return;  // whole warp past the end
+    const bool live = r < a.n_entries;
+    uint32_t off = 0, tiles = 0;
+    if (live) {
+        off = a.offsets[r];
+        const uint32_t next = (r + 1 < a.n_entries) ? a.offsets[r + 1] : (uint32_t)total;
+        tiles = next > off ? next - off : 0u;
+    }
+    if (tiles && (uint64_t)off + tiles > a.cap) set_error(a.err, kErrCapacity);
+    uint4 info = make_uint4(0u, 0u, 0u, 0u);
+    if (tiles) info = a.rinfo[r];
+    const uint32_t rw = info.w & 63u;
+    const uint32_t cnt = rw ? tiles : 0u;  // instances expanded cooperatively
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t excl = incl - cnt;
+    const uint32_t mdiv = rw ? (65536u + rw - 1u) / rw : 0u;  // bit / rw == (bit * mdiv) >> 16 for bit < 32
+    const uint32_t base = off - excl;                          // instance j of the warp lands at base + j
+    for (uint32_t j0 = 0; j0 < wtotal; j0 += 32) {
+        const uint32_t j = j0 + (uint32_t)lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t p = __shfl_sync(0xffffffffu, incl, owner + step - 1);
+            if (p <= j) owner += step;
+        }
+        const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, owner);
+        const uint32_t o_base = __shfl_sync(0xffffffffu, base, owner);
+        const uint32_t o_mask = __shfl_sync(0xffffffffu, info.y, owner);
+        const uint32_t o_org = __shfl_sync(0xffffffffu, info.z, owner);
+        const uint32_t o_shape = __shfl_sync(0xffffffffu, info.w, owner);
+        const uint32_t o_mdiv = __shfl_sync(0xffffffffu, mdiv, owner);
+        const uint32_t o_e = __shfl_sync(0xffffffffu, info.x, owner);
+        if (j < wtotal) {
+            const uint32_t bit = select_bit(o_mask, j - o_excl);
+            const uint32_t row = (bit * o_mdiv) >> 16;
+            const uint32_t col = bit - row * (o_shape & 63u);
+            const uint64_t pos = (uint64_t)o_base + j;
+            if (pos < a.cap) {
+                a.ikey[pos] = o_org + row * (o_shape >> 6) + col;
+                a.ival[pos] = o_e;
+            }
+        }
+    }
+    if (!tiles || rw) return;
+    // a box of more than 32 tiles: per-tile test over the box, row-major
     const uint32_t e = info.x;
     const int v = (int)(e / (uint32_t)a.n);
     const uint32_t tbase = (uint32_t)a.V.tile_base[v];
     const int tiles_x = a.V.tiles_x[v];
-    const int tx0 = (int)(info.z & 0xffffu), ty0 = (int)(info.z >> 16);
-    const int rw = (int)(info.w & 0xffffu), rh = (int)(info.w >> 16);
-    if (rw * rh <= 32) {  // the preprocess kept the hits as a row-major bit mask over the tile box
-        uint32_t m = info.y;
-        while (m) {
-            const int bit = __ffs(m) - 1;
-            m &= m - 1;
-            if (off < a.cap) {
-                a.ikey[off] = tbase + (uint32_t)((ty0 + bit / rw) * tiles_x + tx0 + bit % rw);
-                a.ival[off] = e;
-            }
-            ++off;
-        }
-        return;
-    }
     const uint4 br = a.binrec[2 * (size_t)e];
     const float4 r0 = a.rec[4 * (size_t)e], r1 = a.rec[4 * (size_t)e + 1];
     const float u = r0.x, vv = r0.y, ca = r0.z, cb = r0.w, cc = r1.x;
@@ -313,16 +383,17 @@ __global__ void __launch_bounds__(128) k_emit(EmitArgs a) {
     const int W = a.V.width[v], H = a.V.height[v], tw = a.V.tile_w, th = a.V.tile_h;
     int x0, x1, y0, y1;
     pixel_box(u, vv, ext_x, ext_y, W, H, x0, x1, y0, y1);
+    uint64_t o = off;
     for (int ty = y0 / th; ty <= y1 / th; ++ty) {
         const int py0 = max(ty * th, y0), py1 = min(ty * th + th - 1, y1);
         for (int tx = x0 / tw; tx <= x1 / tw; ++tx) {
             const int px0 = max(tx * tw, x0), px1 = min(tx * tw + tw - 1, x1);
             if (tile_hit(u, vv, ca, cb, cc, ia, ic, qm, px0, px1, py0, py1)) {
-                if (off < a.cap) {
-                    a.ikey[off] = tbase + (uint32_t)(ty * tiles_x + tx);
-                    a.ival[off] = e;
+                if (o < a.cap) {
+                    a.ikey[o] = tbase + (uint32_t)(ty * tiles_x + tx);
+                    a.ival[o] = e;
                 }
-                ++off;
+                ++o;
             }
         }
     }
@@ -399,7 +470,7 @@ cudaError_t launch_bin(const BinArgs &a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const uint32_t *sorted_e = dv[0];  // 4 passes: result back in buffer 0
     // 2. tiles touched in depth order -> exclusive scan -> emission offsets
-    k_gather_counts<<<ceil_div_u64(nE, 128), 128, 0, s>>>(sorted_e, a.binrec, a.rcount, a.rinfo, nE);
+    k_gather_counts<<<ceil_div_u64(nE, 128), 128, 0, s>>>(sorted_e, a.binrec, a.rcount, a.rinfo, nE, a.n, a.V);
     e = exclusive_scan(a.rcount, a.rcount, nE, a.partials, nullptr, s);
     if (e != cudaSuccess) return e;
     k_set_count<<<1, 1, 0, s>>>(a.total, a.cap, a.header);

@@ -338,7 +338,7 @@ struct PreBwdArgs {
 struct EmitArgs {
     uint32_t n_entries;
     int n;  // splats per view
-    const uint4 *rinfo;        // per rank: entry, hit mask, tile box origin, tile box size
+    const uint4 *rinfo;        // per rank: entry, hit mask, key of the box's first tile, box width | tiles_x << 6
     const uint32_t *offsets;   // exclusive scan of tiles touched in that order
     const float4 *rec;
     const uint4 *binrec;
