@@ -54,25 +54,99 @@ __device__ __forceinline__ void load_sh_rgb(const float *color, int K, size_t i,
     r = fmaxf(r, 0.f); g = fmaxf(g, 0.f); b = fmaxf(b, 0.f);
 }
 
-__global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
-    const int NV = a.V.n_views;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long my_tiles = 0;
-    if (t < (long long)a.n * NV) {
-        const int i = (int)(t / NV), v = (int)(t - (long long)i * NV);
-        const size_t e = (size_t)v * a.n + i;
+// Tile tests of a warp's 32 entries, spread over the warp's lanes. Entry (lane) l
+// owns the tests [excl_l, incl_l) of the warp's running count (its box, row-major);
+// each round, lane j takes test j0 + j: the owner is found by a binary search over
+// the inclusive prefix, its ellipse and pixel box come by shuffle, and the hits of
+// the round come back to the owners as one ballot. A splat whose box spans
+// thousands of tiles then costs its warp a share of rounds instead of one lane
+// testing every tile while the other 31 wait. The tile test and the row-major bit
+// order are those of a per-entry loop over the box.
+struct TileJob {
+    float u, v, a, b, c, ia, ic, qm;
+    uint32_t xs, ys;  // x0 | x1 << 16, y0 | y1 << 16 (pixel box, non-empty)
+    uint32_t nbox;    // tiles in the box (0: nothing to test)
+};
+
+__device__ __forceinline__ void warp_tile_tests(const TileJob &J, int lane, int lw, int lh, int tw, int th,
+                                                uint32_t &tiles, uint32_t &mask) {
+    constexpr uint32_t FULL = 0xffffffffu;
+    uint32_t incl = J.nbox;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t wtotal = __shfl_sync(FULL, incl, 31);
+    const uint32_t excl = incl - J.nbox;
+    tiles = 0;
+    mask = 0;
+    for (uint32_t j0 = 0; j0 < wtotal; j0 += 32) {
+        const uint32_t j = j0 + (uint32_t)lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t p = __shfl_sync(FULL, incl, owner + step - 1);
+            if (p <= j) owner += step;
+        }
+        const uint32_t o_excl = __shfl_sync(FULL, excl, owner);
+        const float u = __shfl_sync(FULL, J.u, owner), v = __shfl_sync(FULL, J.v, owner);
+        const float ca = __shfl_sync(FULL, J.a, owner), cb = __shfl_sync(FULL, J.b, owner);
+        const float cc = __shfl_sync(FULL, J.c, owner), ia = __shfl_sync(FULL, J.ia, owner);
+        const float ic = __shfl_sync(FULL, J.ic, owner), qm = __shfl_sync(FULL, J.qm, owner);
+        const uint32_t xs = __shfl_sync(FULL, J.xs, owner), ys = __shfl_sync(FULL, J.ys, owner);
+        bool hit = false;
+        if (j < wtotal) {
+            const int x0 = (int)(xs & 0xffffu), x1 = (int)(xs >> 16);
+            const int y0 = (int)(ys & 0xffffu), y1 = (int)(ys >> 16);
+            const int tx0 = x0 >> lw, ty0 = y0 >> lh;
+            const uint32_t rw = (uint32_t)((x1 >> lw) - tx0 + 1);
+            const uint32_t k = j - o_excl;
+            const uint32_t row = k / rw;
+            const int tx = tx0 + (int)(k - row * rw), ty = ty0 + (int)row;
+            const int px0 = max(tx * tw, x0), px1 = min(tx * tw + tw - 1, x1);
+            const int py0 = max(ty * th, y0), py1 = min(ty * th + th - 1, y1);
+            hit = tile_hit(u, v, ca, cb, cc, ia, ic, qm, px0, px1, py0, py1);
+        }
+        const uint32_t hits = __ballot_sync(FULL, hit);
+        // this lane's tests inside the round: [lo, hi) of the warp's count
+        const uint32_t lo = max(excl, j0), hi = min(incl, j0 + 32u);
+        if (lo < hi) {
+            const uint32_t len = hi - lo;
+            const uint32_t bits = (hits >> (lo - j0)) & (len == 32u ? FULL : ((1u << len) - 1u));
+            tiles += (uint32_t)__popc(bits);
+            if (lo - excl < 32u) mask |= bits << (lo - excl);  // bits of tests 32 and beyond drop out
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {
+    const uint32_t NV = (uint32_t)a.V.n_views;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;  // n * NV < 2^31 (host check)
+    const int lane = threadIdx.x & 31;
+    const bool live = t < (uint32_t)a.n * NV;
+    const int tw = a.V.tile_w, th = a.V.tile_h;
+    const int lw = __ffs(tw) - 1, lh = __ffs(th) - 1;  // tile sides are powers of two
+    uint32_t i = 0, v = 0;
+    size_t e = 0;
+    float z32 = 0.f, ext_x = 0.f, ext_y = 0.f;
+    bool visible = false;
+    TileJob J = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, 0u};
+    uint32_t rect = 0, rdim = 0;
+    if (live) {
+        i = t / NV;
+        v = t - i * NV;
+        e = (size_t)v * a.n + i;
         const float4 po = __ldg(a.pos_op + i);
         const float4 ls = __ldg(a.lsb + i);
         const float4 q4 = __ldg(a.quat + i);
         const float o = po.w, beta = ls.w;
         const float *vm = a.V.vm[v];
-        const float z32 = depth32(vm, po.x, po.y, po.z);
-        uint32_t tiles = 0, mask = 0, rect = 0, rdim = 0;
+        z32 = depth32(vm, po.x, po.y, po.z);
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
-        float ext_x = 0.f, ext_y = 0.f;
         const bool op_ok = o >= a.P.alpha_min;
-        bool visible = op_ok && isfinite(po.x) && isfinite(po.y) && isfinite(po.z) && isfinite(beta) && beta > 0.f &&
-                       z32 > a.V.znear[v];
+        visible = op_ok && isfinite(po.x) && isfinite(po.y) && isfinite(po.z) && isfinite(beta) && beta > 0.f &&
+                  z32 > a.V.znear[v];
         if (visible) {
             const float qinv = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
             float R[9];
@@ -127,26 +201,16 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
             } else {
                 ext_x = sqrtf(__fmul_rn(A, qm));
                 ext_y = sqrtf(__fmul_rn(C, qm));
-                // tile overlap (S3): pixel box, then the ellipse-rectangle test per tile;
-                // for boxes of at most 32 tiles the hits are kept as a bit mask for emission
-                const int W = a.V.width[v], H = a.V.height[v], tw = a.V.tile_w, th = a.V.tile_h;
+                // tile overlap (S3): the pixel box here, the ellipse-rectangle test per tile
+                // of the box below (whole warp)
                 int x0, x1, y0, y1;
-                pixel_box(u, vv, ext_x, ext_y, W, H, x0, x1, y0, y1);
+                pixel_box(u, vv, ext_x, ext_y, a.V.width[v], a.V.height[v], x0, x1, y0, y1);
                 if (x0 <= x1 && y0 <= y1) {
-                    const int tx0 = x0 / tw, tx1 = x1 / tw, ty0 = y0 / th, ty1 = y1 / th;
+                    const int tx0 = x0 >> lw, tx1 = x1 >> lw, ty0 = y0 >> lh, ty1 = y1 >> lh;
                     const int rw = tx1 - tx0 + 1, rh = ty1 - ty0 + 1;
-                    const float ia = __frcp_rn(ca), ic = __frcp_rn(cc);
-                    int bit = 0;
-                    for (int ty_ = ty0; ty_ <= ty1; ++ty_) {
-                        const int py0 = max(ty_ * th, y0), py1 = min(ty_ * th + th - 1, y1);
-                        for (int tx_ = tx0; tx_ <= tx1; ++tx_, ++bit) {
-                            const int px0 = max(tx_ * tw, x0), px1 = min(tx_ * tw + tw - 1, x1);
-                            if (tile_hit(u, vv, ca, cb, cc, ia, ic, qm, px0, px1, py0, py1)) {
-                                ++tiles;
-                                if (bit < 32) mask |= 1u << bit;
-                            }
-                        }
-                    }
+                    J = TileJob{u, vv, ca, cb, cc, __frcp_rn(ca), __frcp_rn(cc), qm,
+                                (uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16),
+                                (uint32_t)rw * (uint32_t)rh};
                     rect = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
                     rdim = (uint32_t)rw | ((uint32_t)rh << 16);
                 }
@@ -184,18 +248,23 @@ __global__ void __launch_bounds__(256) k_preprocess(PreArgs a) {
         a.rec[4 * e + 1] = r1;
         a.rec[4 * e + 2] = r2;
         a.rec[4 * e + 3] = r3;
+    }
+    uint32_t tiles, mask;
+    warp_tile_tests(J, lane, lw, lh, tw, th, tiles, mask);
+    unsigned long long my_tiles = 0;
+    if (live) {
         const bool listed = visible && tiles > 0;
         const uint32_t key = listed ? __float_as_uint(z32) : kCulledKey;
         a.binrec[2 * e] = make_uint4(__float_as_uint(ext_x), __float_as_uint(ext_y), listed ? tiles : 0u, key);
         a.binrec[2 * e + 1] = make_uint4(mask, rect, rdim, 0u);
-        my_tiles += listed ? tiles : 0u;
+        my_tiles = listed ? tiles : 0u;
     }
     // block reduction of the tile count, one atomic per CTA
     __shared__ unsigned long long s_sum[8];
     unsigned long long tsum = my_tiles;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) tsum += __shfl_down_sync(0xffffffffu, tsum, off);
-    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = tsum;
+    if (lane == 0) s_sum[threadIdx.x >> 5] = tsum;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long sum = 0;
