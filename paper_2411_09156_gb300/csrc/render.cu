@@ -256,29 +256,33 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
         const float rx0 = (float)(tx0 + wx0) + 0.5f, rx1 = rx0 + (float)(kWarpW - 1);
         const float ry0 = (float)(ty0 + wy0) + 0.5f, ry1 = ry0 + (float)(kWarpH - 1);
         const uint2 rg = a.ranges[tile];
-        // per-pixel forward results and upstream gradients
-        float Tend = 1.f, Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f, Df = 0.f, Nf0 = 0.f, Nf1 = 0.f, Nf2 = 0.f;
-        float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f, gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
+        // per-pixel forward results F_k and upstream gradients g_k of the 7 blended
+        // channels (colour, depth, normal), and g_alpha T_final
+        float Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f, Df = 0.f, Nf0 = 0.f, Nf1 = 0.f, Nf2 = 0.f, gAT = 0.f;
+        float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
         uint32_t lp = rg.x;
         if (inside) {
             const long long P = (long long)W * H;
             const long long pix = (long long)py * W + px;
             const long long g = a.V.pix_base[v] + pix;
             const long long c3 = 3 * a.V.pix_base[v] + pix;
-            Tend = a.t_final[g];
             lp = a.last[g];
             if (a.g_color) {
                 gC0 = a.g_color[c3]; gC1 = a.g_color[c3 + P]; gC2 = a.g_color[c3 + 2 * P];
                 Cf0 = a.color[c3]; Cf1 = a.color[c3 + P]; Cf2 = a.color[c3 + 2 * P];
             }
             if (a.g_depth) { gD = a.g_depth[g]; Df = a.depth[g]; }
-            if (a.g_alpha) gA = a.g_alpha[g];
+            if (a.g_alpha) gAT = a.g_alpha[g] * a.t_final[g];
             if (a.g_normal) {
                 gN0 = a.g_normal[c3]; gN1 = a.g_normal[c3 + P]; gN2 = a.g_normal[c3 + 2 * P];
                 Nf0 = a.normal[c3]; Nf1 = a.normal[c3 + P]; Nf2 = a.normal[c3 + 2 * P];
             }
         }
         const uint32_t wend = __reduce_max_sync(0xffffffffu, lp);  // this warp replays [rg.x, wend)
+        // transmittance before splat i and the channels accumulated up to and including
+        // splat i, A_k, in the forward pass's operation order: F_k - A_k, the part of the
+        // pixel behind splat i, is then exact at the last splat and carries only the
+        // rounding of the later steps
         float T = 1.f, Ca0 = 0.f, Ca1 = 0.f, Ca2 = 0.f, Da = 0.f, Na0 = 0.f, Na1 = 0.f, Na2 = 0.f;
         uint32_t e_cur = entry_or_none(a.inst_entry, rg.x + lane, wend);
         uint32_t e_pf = entry_or_none(a.inst_entry, rg.x + ahead + lane, wend);
@@ -314,13 +318,13 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
                         Na0 = __fmaf_rn(w, r3.x, Na0);
                         Na1 = __fmaf_rn(w, r3.y, Na1);
                         Na2 = __fmaf_rn(w, r3.z, Na2);
-                        const float inv = 1.f / (1.f - al);
-                        float dal = gC0 * (T * r2.x - (Cf0 - Ca0) * inv) + gC1 * (T * r2.y - (Cf1 - Ca1) * inv) +
-                                    gC2 * (T * r2.z - (Cf2 - Ca2) * inv);
-                        dal += gD * (T * r2.w - (Df - Da) * inv);
-                        dal += gN0 * (T * r3.x - (Nf0 - Na0) * inv) + gN1 * (T * r3.y - (Nf1 - Na1) * inv) +
-                               gN2 * (T * r3.z - (Nf2 - Na2) * inv);
-                        dal += gA * Tend * inv;
+                        // d out / d alpha_i = T_i sum_k g_k c_ik - (sum_k g_k (F_k - A_k) - g_alpha T_final) / (1 - alpha_i)
+                        const float gc = gC0 * r2.x + gC1 * r2.y + gC2 * r2.z + gD * r2.w + gN0 * r3.x +
+                                         gN1 * r3.y + gN2 * r3.z;
+                        const float behind = gC0 * (Cf0 - Ca0) + gC1 * (Cf1 - Ca1) + gC2 * (Cf2 - Ca2) +
+                                             gD * (Df - Da) + gN0 * (Nf0 - Na0) + gN1 * (Nf1 - Na1) +
+                                             gN2 * (Nf2 - Na2);
+                        const float dal = T * gc - (behind - gAT) * rcp_approx(1.f - al);
                         T = __fmul_rn(T, __fsub_rn(1.f, al));
                         const float o = r1.w, hb = r1.z;
                         float gG = 0.f;
@@ -328,22 +332,23 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
                             g[5] = dal * pe.G;
                             gG = dal * o;
                         }
-                        float dGdQ = 0.f, dGdb = 0.f;
+                        // G = exp(-p/2), p = Q^(beta/2): dG/dQ = -(beta/4) (p/Q) G, dG/dbeta = -(1/4) p ln(Q) G
+                        float gQ = 0.f;
                         if (pe.Q > 0.f) {
-                            dGdQ = -0.5f * hb * __fdividef(pe.p, pe.Q) * pe.G;
-                            dGdb = -0.25f * pe.p * (lg2_approx(pe.Q) * ln2) * pe.G;
+                            const float gp = gG * pe.p * pe.G;
+                            gQ = -0.5f * hb * gp * rcp_approx(pe.Q);
+                            g[6] = -0.25f * ln2 * gp * lg2_approx(pe.Q);
                         }
                         // Q = d^T C d with C = Sigma'^-1 and d = pixel - mean; with m = C d:
                         // dQ/dmean = -2 m and dQ/dSigma' = -m m^T (accumulated directly:
                         // going through the conic gradient would cancel for thin splats)
-                        const float gQ = gG * dGdQ;
                         const float mx = fmaf(r0.z, dx, 0.5f * r0.w * dy), my = fmaf(0.5f * r0.w, dx, r1.x * dy);
-                        g[0] = -2.f * gQ * mx;
-                        g[1] = -2.f * gQ * my;
-                        g[2] = -gQ * mx * mx;
-                        g[3] = -gQ * mx * my;
-                        g[4] = -gQ * my * my;
-                        g[6] = gG * dGdb;
+                        const float qx = -gQ * mx, qy = -gQ * my;
+                        g[0] = 2.f * qx;
+                        g[1] = 2.f * qy;
+                        g[2] = qx * mx;
+                        g[3] = qx * my;
+                        g[4] = qy * my;
                         g[7] = gD * w;
                         g[8] = gC0 * w;
                         g[9] = gC1 * w;
