@@ -18,6 +18,7 @@ scaling, no collective on the data path); the reported time is the max over rank
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -49,6 +50,8 @@ def parse_args():
     p.add_argument("--no-per-view", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--tile", default=None, help="fix the tile shape, WxH (skips the autotuner)")
+    p.add_argument("--batch", type=int, default=None, help="fix the prefetch distance (skips the autotuner)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the oracle sample")
     p.add_argument("--splats", type=int, default=None,
@@ -158,7 +161,15 @@ def upstream_grads(P: int, seed: int):
     return [torch.randn(n, generator=g, device="cuda") for n in (3 * P, P, P, 3 * P)]
 
 
-def profile_traffic(kernel: str, src_file: str):
+def kernel_source_sha256() -> str:
+    """sha256 of the render kernels' sources (render.cu followed by ges_internal.cuh)."""
+    h = hashlib.sha256()
+    for f in ("render.cu", "ges_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2411_09156_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def profile_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current source."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_drt8-1.5M.md")
     if not os.path.exists(path):
@@ -166,7 +177,7 @@ def profile_traffic(kernel: str, src_file: str):
     txt = open(path).read()
     m = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
     b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    cur = hashlib.sha256(open(src_file, "rb").read()).hexdigest()
+    cur = kernel_source_sha256()
     if not m or not b or m.group(1) != cur:
         return None, cur
     return float(b.group(1)), cur
@@ -261,7 +272,11 @@ def main():
     P = sum(c.width * c.height for c in cams)
     ups = upstream_grads(P, 1000 + rank)
     base = api.GESConfig(sh_degree=sc.sh_degree, persistent=1)
-    cfg = base if args.no_autotune else autotune(sc.n, cams, base, inputs, ups, key=args.workload)
+    if args.tile or args.batch:
+        tw, th = (int(x) for x in (args.tile or f"{base.tile_w}x{base.tile_h}").split("x"))
+        cfg = dataclasses.replace(base, tile_w=tw, tile_h=th, batch=args.batch or base.batch)
+    else:
+        cfg = base if args.no_autotune else autotune(sc.n, cams, base, inputs, ups, key=args.workload)
     plan = BatchPlan(sc.n, cams, cfg, inputs, ups)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
 
@@ -330,7 +345,7 @@ def main():
     if names[dom] in kernels:
         kname, fl = kernels[names[dom]]
         achieved = fl / (stage_avg[dom] / 1e3) / 1e12
-        traffic, _ = profile_traffic(kname, os.path.join(ROOT, "paper_2411_09156_gb300", "csrc", "render.cu"))
+        traffic, _ = profile_traffic(kname)
         roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": achieved / fp32_peak, "traffic": traffic,
                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled median)",

@@ -4,6 +4,7 @@
 // runs without a host round trip and can be captured in a CUDA graph with
 // capacity-sized grids (CTAs past the live count exit at once).
 #include "ges_internal.cuh"
+#include "tile_tests.cuh"
 
 namespace ges {
 
@@ -368,35 +369,53 @@ __global__ void __launch_bounds__(128) k_emit(EmitArgs a) {
             }
         }
     }
-    if (!tiles || rw) return;
-    // a box of more than 32 tiles: per-tile test over the box, row-major
-    const uint32_t e = info.x;
-    const int v = (int)(e / (uint32_t)a.n);
-    const uint32_t tbase = (uint32_t)a.V.tile_base[v];
-    const int tiles_x = a.V.tiles_x[v];
-    const uint4 br = a.binrec[2 * (size_t)e];
-    const float4 r0 = a.rec[4 * (size_t)e], r1 = a.rec[4 * (size_t)e + 1];
-    const float u = r0.x, vv = r0.y, ca = r0.z, cb = r0.w, cc = r1.x;
-    const float qm = __fmul_rn(r1.y, kSupportMargin);
-    const float ia = __frcp_rn(ca), ic = __frcp_rn(cc);
-    const float ext_x = __uint_as_float(br.x), ext_y = __uint_as_float(br.y);
-    const int W = a.V.width[v], H = a.V.height[v], tw = a.V.tile_w, th = a.V.tile_h;
-    int x0, x1, y0, y1;
-    pixel_box(u, vv, ext_x, ext_y, W, H, x0, x1, y0, y1);
-    uint64_t o = off;
-    for (int ty = y0 / th; ty <= y1 / th; ++ty) {
-        const int py0 = max(ty * th, y0), py1 = min(ty * th + th - 1, y1);
-        for (int tx = x0 / tw; tx <= x1 / tw; ++tx) {
-            const int px0 = max(tx * tw, x0), px1 = min(tx * tw + tw - 1, x1);
-            if (tile_hit(u, vv, ca, cb, cc, ia, ic, qm, px0, px1, py0, py1)) {
-                if (o < a.cap) {
-                    a.ikey[o] = tbase + (uint32_t)(ty * tiles_x + tx);
-                    a.ival[o] = e;
-                }
-                ++o;
-            }
-        }
+    // boxes of more than 32 tiles: the tile tests spread over the warp, each hit
+    // written at its entry's offset plus the number of earlier hits of that entry
+    // (row-major order, as a per-entry loop over the box would write them)
+    const bool big = tiles && !rw;
+    if (!__any_sync(0xffffffffu, big)) return;
+    const int tw = a.V.tile_w, th = a.V.tile_h;
+    const int lw = __ffs(tw) - 1, lh = __ffs(th) - 1;  // tile sides are powers of two
+    TileJob J = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, 0u};
+    uint32_t tbase = 0;
+    int tiles_x = 0;
+    if (big) {
+        const uint32_t e = info.x;
+        const int v = (int)(e / (uint32_t)a.n);
+        tbase = (uint32_t)a.V.tile_base[v];
+        tiles_x = a.V.tiles_x[v];
+        const uint4 br = a.binrec[2 * (size_t)e];
+        const float4 r0 = a.rec[4 * (size_t)e], r1 = a.rec[4 * (size_t)e + 1];
+        int x0, x1, y0, y1;
+        pixel_box(r0.x, r0.y, __uint_as_float(br.x), __uint_as_float(br.y), a.V.width[v], a.V.height[v], x0, x1,
+                  y0, y1);
+        if (x0 <= x1 && y0 <= y1)
+            J = TileJob{r0.x, r0.y, r0.z, r0.w, r1.x, __frcp_rn(r0.z), __frcp_rn(r1.x), __fmul_rn(r1.y, kSupportMargin),
+                        (uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16),
+                        (uint32_t)((x1 >> lw) - (x0 >> lw) + 1) * (uint32_t)((y1 >> lh) - (y0 >> lh) + 1)};
     }
+    uint32_t written = 0;  // hits of this lane's entry written so far
+    warp_tile_rounds(J, lane, lw, lh, tw, th,
+                     [&](uint32_t hits, uint32_t lo, uint32_t len, uint32_t, int tx, int ty, uint32_t owner,
+                         bool hit) {
+                         const uint32_t o_off = __shfl_sync(0xffffffffu, off, owner);
+                         const uint32_t o_written = __shfl_sync(0xffffffffu, written, owner);
+                         const uint32_t o_tbase = __shfl_sync(0xffffffffu, tbase, owner);
+                         const int o_tiles_x = __shfl_sync(0xffffffffu, tiles_x, owner);
+                         const uint32_t o_e = __shfl_sync(0xffffffffu, info.x, owner);
+                         const uint32_t same = __match_any_sync(0xffffffffu, owner);
+                         if (hit) {
+                             const uint64_t pos = (uint64_t)o_off + o_written +
+                                                  (uint32_t)__popc(hits & same & ((1u << lane) - 1u));
+                             if (pos < a.cap) {
+                                 a.ikey[pos] = o_tbase + (uint32_t)(ty * o_tiles_x + tx);
+                                 a.ival[pos] = o_e;
+                             }
+                         }
+                         if (len)
+                             written += (uint32_t)__popc((hits >> lo) &
+                                                         (len == 32u ? 0xffffffffu : ((1u << len) - 1u)));
+                     });
 }
 
 // n_inst = min(total, cap); 0 when the total does not fit the uint32 offsets

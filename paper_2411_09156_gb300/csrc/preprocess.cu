@@ -3,6 +3,7 @@
 // read once with float4 loads and every view is processed from registers, so a
 // batch of V views reads the splat parameters once instead of V times.
 #include "ges_internal.cuh"
+#include "tile_tests.cuh"
 
 namespace ges {
 
@@ -54,70 +55,20 @@ __device__ __forceinline__ void load_sh_rgb(const float *color, int K, size_t i,
     r = fmaxf(r, 0.f); g = fmaxf(g, 0.f); b = fmaxf(b, 0.f);
 }
 
-// Tile tests of a warp's 32 entries, spread over the warp's lanes. Entry (lane) l
-// owns the tests [excl_l, incl_l) of the warp's running count (its box, row-major);
-// each round, lane j takes test j0 + j: the owner is found by a binary search over
-// the inclusive prefix, its ellipse and pixel box come by shuffle, and the hits of
-// the round come back to the owners as one ballot. A splat whose box spans
-// thousands of tiles then costs its warp a share of rounds instead of one lane
-// testing every tile while the other 31 wait. The tile test and the row-major bit
-// order are those of a per-entry loop over the box.
-struct TileJob {
-    float u, v, a, b, c, ia, ic, qm;
-    uint32_t xs, ys;  // x0 | x1 << 16, y0 | y1 << 16 (pixel box, non-empty)
-    uint32_t nbox;    // tiles in the box (0: nothing to test)
-};
-
+// Tile tests of a warp's 32 entries, spread over the warp's lanes (see
+// warp_tile_rounds): each lane collects its own entry's hit count and, for the
+// first 32 tests of its box, the row-major hit mask.
 __device__ __forceinline__ void warp_tile_tests(const TileJob &J, int lane, int lw, int lh, int tw, int th,
                                                 uint32_t &tiles, uint32_t &mask) {
-    constexpr uint32_t FULL = 0xffffffffu;
-    uint32_t incl = J.nbox;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t t = __shfl_up_sync(FULL, incl, d);
-        if (lane >= d) incl += t;
-    }
-    const uint32_t wtotal = __shfl_sync(FULL, incl, 31);
-    const uint32_t excl = incl - J.nbox;
     tiles = 0;
     mask = 0;
-    for (uint32_t j0 = 0; j0 < wtotal; j0 += 32) {
-        const uint32_t j = j0 + (uint32_t)lane;
-        int owner = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const uint32_t p = __shfl_sync(FULL, incl, owner + step - 1);
-            if (p <= j) owner += step;
-        }
-        const uint32_t o_excl = __shfl_sync(FULL, excl, owner);
-        const float u = __shfl_sync(FULL, J.u, owner), v = __shfl_sync(FULL, J.v, owner);
-        const float ca = __shfl_sync(FULL, J.a, owner), cb = __shfl_sync(FULL, J.b, owner);
-        const float cc = __shfl_sync(FULL, J.c, owner), ia = __shfl_sync(FULL, J.ia, owner);
-        const float ic = __shfl_sync(FULL, J.ic, owner), qm = __shfl_sync(FULL, J.qm, owner);
-        const uint32_t xs = __shfl_sync(FULL, J.xs, owner), ys = __shfl_sync(FULL, J.ys, owner);
-        bool hit = false;
-        if (j < wtotal) {
-            const int x0 = (int)(xs & 0xffffu), x1 = (int)(xs >> 16);
-            const int y0 = (int)(ys & 0xffffu), y1 = (int)(ys >> 16);
-            const int tx0 = x0 >> lw, ty0 = y0 >> lh;
-            const uint32_t rw = (uint32_t)((x1 >> lw) - tx0 + 1);
-            const uint32_t k = j - o_excl;
-            const uint32_t row = k / rw;
-            const int tx = tx0 + (int)(k - row * rw), ty = ty0 + (int)row;
-            const int px0 = max(tx * tw, x0), px1 = min(tx * tw + tw - 1, x1);
-            const int py0 = max(ty * th, y0), py1 = min(ty * th + th - 1, y1);
-            hit = tile_hit(u, v, ca, cb, cc, ia, ic, qm, px0, px1, py0, py1);
-        }
-        const uint32_t hits = __ballot_sync(FULL, hit);
-        // this lane's tests inside the round: [lo, hi) of the warp's count
-        const uint32_t lo = max(excl, j0), hi = min(incl, j0 + 32u);
-        if (lo < hi) {
-            const uint32_t len = hi - lo;
-            const uint32_t bits = (hits >> (lo - j0)) & (len == 32u ? FULL : ((1u << len) - 1u));
-            tiles += (uint32_t)__popc(bits);
-            if (lo - excl < 32u) mask |= bits << (lo - excl);  // bits of tests 32 and beyond drop out
-        }
-    }
+    warp_tile_rounds(J, lane, lw, lh, tw, th,
+                     [&](uint32_t hits, uint32_t lo, uint32_t len, uint32_t first, int, int, uint32_t, bool) {
+                         if (!len) return;
+                         const uint32_t bits = (hits >> lo) & (len == 32u ? 0xffffffffu : ((1u << len) - 1u));
+                         tiles += (uint32_t)__popc(bits);
+                         if (first < 32u) mask |= bits << first;  // bits of tests 32 and beyond drop out
+                     });
 }
 
 __global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {

@@ -54,10 +54,9 @@ def test_preprocess_matches_oracle():
 
 
 # ----------------------------------------------------------------- S5: bit-exact keys and order
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
-def test_binning_is_bit_exact(tile):
-    sc, _ = _tiny()
-    cams = [look_at((0.3, -3.6, 0.8), (0, 0, 0), 131, 97), look_at((-1.0, -3.0, 0.5), (0, 0, 0), 64, 80)]
+def _check_binning(sc, cams, tile):
+    """Bit-exact tile counts, (tile, entry) instances in order, and tile ranges against the oracle's
+    float32 integer stage; returns the per-entry tile-box sizes."""
     cfg = api.GESConfig(tile_w=tile[0], tile_h=tile[1])
     rast, _ = H.gpu_forward(sc, cams, cfg)
     pv = rast.proj_views()
@@ -78,6 +77,28 @@ def test_binning_is_bit_exact(tile):
     np.testing.assert_array_equal(bv["entry"].cpu().numpy(), ents)
     np.testing.assert_array_equal(bv["ranges"].cpu().numpy(), ranges)
     assert rast.sync_status() == 0
+    rdim = binrec[:, 6].astype(np.int64)
+    return np.where(vis, (rdim & 0xFFFF) * (rdim >> 16), 0)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
+def test_binning_is_bit_exact(tile):
+    sc, _ = _tiny()
+    cams = [look_at((0.3, -3.6, 0.8), (0, 0, 0), 131, 97), look_at((-1.0, -3.0, 0.5), (0, 0, 0), 64, 80)]
+    _check_binning(sc, cams, tile)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_binning_bit_exact_with_boxes_over_32_tiles(tile):
+    """One splat in twenty scaled up 7.4x: boxes of hundreds of tiles next to boxes of one, so the
+    warps' tile tests and emission run many rounds and the no-mask emission path is exercised."""
+    sc = make_scene(1000, 11, "uniform")
+    big = np.random.default_rng(12).random(sc.n) < 0.05
+    sc.lscale_beta = sc.lscale_beta.copy()
+    sc.lscale_beta[big, :3] += 2.0
+    cams = [look_at((0.3, -3.6, 0.8), (0, 0, 0), 320, 240), look_at((-1.0, -3.0, 0.5), (0, 0, 0), 160, 120)]
+    box = _check_binning(sc, cams, tile)
+    assert (box > 32).sum() >= 10 and box.max() > 256
 
 
 # ----------------------------------------------------------------- S6
@@ -258,3 +279,34 @@ def test_full_size_drt8_batch_sampled_forward():
         px = _sample_pixels(rng, w, h, 48)
         rep, _, _ = H.compare_forward(rast, sc, cams, cfg, v=v, pixels=px)
         assert rep["flagged"] <= 3
+
+
+def test_full_size_drt16_3m_batch_sampled_fwd_bwd():
+    """3M splats, 16 views (480x270 .. 1920x1080 by the cosine schedule), one batched persistent launch:
+    sampled pixels of three views against the oracle, and the gradient from sampled pixels of the
+    largest view (upstream zero everywhere else, so the batched backward sums that view alone)."""
+    sizes = drt_sizes(1920, 1080, 16)
+    sc, cams = workload("drt16-3M", sizes=sizes)
+    cfg = api.GESConfig(sh_degree=3, persistent=1)
+    rast, t = H.gpu_forward(sc, cams, cfg)
+    rng = np.random.default_rng(2)
+    for v in (0, 8):
+        w, h = sizes[v]
+        rep, _, _ = H.compare_forward(rast, sc, cams, cfg, v=v, pixels=_sample_pixels(rng, w, h, 32))
+        assert rep["flagged"] <= 2
+    v = 15
+    w, h = sizes[v]
+    px = _sample_pixels(rng, w, h, 128)
+    rep, ref, _ = H.compare_forward(rast, sc, cams, cfg, v=v, pixels=px)
+    assert rep["flagged"] <= 3
+    keep = [np.zeros(sw * sh, bool) for (sw, sh) in sizes]
+    keep[v][(px[:, 1] * w + px[:, 0])[H.grad_mask(ref)]] = True
+    ups = H.mask_upstream(rast, H.upstream(rast, 1004), keep)
+    grads = rast.backward(*t, *ups)
+    torch.cuda.synchronize()
+    got = {k: x.double().cpu().numpy() for k, x in grads.items()}
+    oc, od, oa, on = H.oracle_upstream(rast, ups, v, pixels=px)
+    refg = O.backward(sc, cams[v].as_dict(), H.oracle_cfg(cfg), oc, od, oa, on, pixels=px)
+    rows = np.nonzero(np.abs(refg["g_pos_op"]).sum(1) + np.abs(got["g_pos_op"]).sum(1) > 0)[0]
+    assert len(rows) > 50
+    H.compare_grads(got, refg, rows=rows)
