@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *key
 }
 
 // Stable scatter: each warp ranks a contiguous 512-key chunk in rounds of 32 with
-// match.any, keeping a per-warp running count per digit; warps are then ordered by
+// digit ballots, keeping a per-warp running count per digit; warps are then ordered by
 // an exclusive prefix per digit. The CTA's 4096 pairs are first reordered by digit
 // in shared memory, then written out in digit runs (coalesced) at the offsets of
 // the scanned digit-major histogram.
@@ -199,7 +199,15 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(const uint32_
         const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
         const bool valid = idx < n;
         const uint32_t d = (key[r] >> shift) & 0xffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
+        // lanes holding the same digit (invalid lanes carry 0x100): one ballot per digit
+        // bit, which issues faster than match.any on spread-out digits
+        const uint32_t dd = valid ? d : 0x100u;
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, (dd >> b) & 1u);
+            peers &= ((dd >> b) & 1u) ? bal : ~bal;
+        }
         uint32_t before = 0;
         if (valid) before = s_cnt[warp][d];
         __syncwarp();

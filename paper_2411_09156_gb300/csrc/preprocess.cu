@@ -238,13 +238,19 @@ __device__ __forceinline__ float seg_sum(float x, int width) {
 }
 
 // Recursive-halving sum of 48 values over a segment of SEG lanes (compile-time
-// sizes keep every index static, so the values stay in registers); each lane ends
-// with 48/SEG of the sums and writes the ones that exist (k < K).
+// sizes keep every index static, so the values stay in registers): at each level a
+// lane keeps half of its values and adds its partner's copy of them, so 48 values
+// cost 24 + 12 + ... shuffles instead of 48 per level. 48 = 3 x 16 halves four
+// times; with 32 lanes the fifth level adds the 3 remaining values outright and
+// the even lane of each pair writes. Lane v writes the sums it holds, values
+// [base, base + CNT), that exist (index < 3K).
 template <int SEG>
 __device__ __forceinline__ void write_sh_grad(float (&t)[48], int v, int K, bool ok, float *gcol) {
+    constexpr int HALVINGS = SEG >= 16 ? 4 : (SEG == 8 ? 3 : (SEG == 4 ? 2 : (SEG == 2 ? 1 : 0)));
+    constexpr int CNT = 48 >> HALVINGS;
     int base = 0;
 #pragma unroll
-    for (int o = SEG >> 1, cnt = 48; o > 0; o >>= 1, cnt >>= 1) {
+    for (int l = 0, o = SEG >> 1, cnt = 48; l < HALVINGS; ++l, o >>= 1, cnt >>= 1) {
         const int h = cnt >> 1;
         const bool up = (v & o) != 0;
 #pragma unroll
@@ -255,8 +261,11 @@ __device__ __forceinline__ void write_sh_grad(float (&t)[48], int v, int K, bool
         }
         if (up) base += h;
     }
-    constexpr int CNT = 48 / SEG;
-    if (ok) {
+    if (SEG == 32) {
+#pragma unroll
+        for (int q = 0; q < CNT; ++q) t[q] += __shfl_xor_sync(0xffffffffu, t[q], 1);
+    }
+    if (ok && (SEG < 32 || (v & 1) == 0)) {
 #pragma unroll
         for (int q = 0; q < CNT; ++q)
             if (base + q < K * 3) gcol[base + q] = t[q];
@@ -269,10 +278,10 @@ __device__ __forceinline__ void write_sh_grad(float (&t)[48], int v, int K, bool
 // views are formed with shuffles inside the segment. Lane 0 of the segment
 // writes the geometry gradients; the SH coefficient gradients are written by all
 // lanes of the segment, coefficient k by lane k mod seg.
-__global__ void __launch_bounds__(256) k_preprocess_bwd(PreBwdArgs a) {
+template <int SEG>
+__global__ void __launch_bounds__(256, 3) k_preprocess_bwd(PreBwdArgs a) {
     const int NV = a.V.n_views;
-    int seg = 1;
-    while (seg < NV) seg <<= 1;
+    constexpr int seg = SEG;  // lanes per splat: the view count rounded up to a power of two
     const int lane = threadIdx.x & 31;
     const int spw = 32 / seg;  // splats per warp
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -471,21 +480,11 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(PreBwdArgs a) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) Y[k] = 0.f;
     if (has) sh_eval(a.P.sh_degree, sdir[0], sdir[1], sdir[2], Y);
-    // the 48 products wc_c Y_k summed over the segment's lanes by recursive halving:
-    // at each level a lane keeps half of its values and adds its partner's copy of
-    // them, so 48 values cost 24 + 12 + ... shuffles instead of 48 per level
+    // the 48 products wc_c Y_k summed over the segment's lanes
     float t[48];
 #pragma unroll
     for (int k = 0; k < 16; ++k) { t[3 * k] = wc[0] * Y[k]; t[3 * k + 1] = wc[1] * Y[k]; t[3 * k + 2] = wc[2] * Y[k]; }
-    float *gcol = a.g_color + (size_t)i * K * 3;
-    switch (seg) {
-        case 1: write_sh_grad<1>(t, v, K, splat_ok, gcol); break;
-        case 2: write_sh_grad<2>(t, v, K, splat_ok, gcol); break;
-        case 4: write_sh_grad<4>(t, v, K, splat_ok, gcol); break;
-        case 8: write_sh_grad<8>(t, v, K, splat_ok, gcol); break;
-        case 16: write_sh_grad<16>(t, v, K, splat_ok, gcol); break;
-        default: write_sh_grad<32>(t, v, K, splat_ok, gcol); break;
-    }
+    write_sh_grad<SEG>(t, v, K, splat_ok, a.g_color + (size_t)i * K * 3);
 }
 
 cudaError_t launch_preprocess(const PreArgs &a, cudaStream_t s) {
@@ -501,7 +500,15 @@ cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t s) {
     while (seg < a.V.n_views) seg <<= 1;
     const long long warps = ((long long)a.n + (32 / seg) - 1) / (32 / seg);
     const size_t smem = a.P.sh_degree >= 0 ? (size_t)8 * (32 / seg) * a.P.n_coeffs * 3 * sizeof(float) : 0;
-    k_preprocess_bwd<<<(unsigned)((warps * 32 + 255) / 256), 256, smem, s>>>(a);
+    const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+    switch (seg) {
+        case 1: k_preprocess_bwd<1><<<grid, 256, smem, s>>>(a); break;
+        case 2: k_preprocess_bwd<2><<<grid, 256, smem, s>>>(a); break;
+        case 4: k_preprocess_bwd<4><<<grid, 256, smem, s>>>(a); break;
+        case 8: k_preprocess_bwd<8><<<grid, 256, smem, s>>>(a); break;
+        case 16: k_preprocess_bwd<16><<<grid, 256, smem, s>>>(a); break;
+        default: k_preprocess_bwd<32><<<grid, 256, smem, s>>>(a); break;
+    }
     return cudaGetLastError();
 }
 

@@ -200,13 +200,18 @@ def test_tile_shapes_batches_and_persistent_are_bit_identical():
             assert torch.equal(out[k], base[k]), (cfg, k)
 
 
-def test_batched_views_equal_per_view_calls():
-    sc = make_scene(5000, 51, "heightfield", 2)
-    sizes = drt_sizes(160, 104, 4)
+@pytest.mark.parametrize("n_views,sh_degree", [(4, 2), (5, 3), (20, 3)])
+def test_batched_views_equal_per_view_calls(n_views, sh_degree):
+    """The batched launch gives each view the image of a one-view call, and the sum of the one-view
+    gradients; 5 views leave idle lanes in the backward's 8-lane view segments, 20 views use
+    32-lane segments."""
+    sc = make_scene(5000, 51, "heightfield", sh_degree)
+    sizes = drt_sizes(160, 104, n_views)
     rng = np.random.default_rng(7)
-    cams = [look_at(5.0 * d / np.linalg.norm(d), (0, 0, 0), w, h) for d, (w, h) in zip(rng.normal(size=(4, 3)), sizes)]
+    cams = [look_at(5.0 * d / np.linalg.norm(d), (0, 0, 0), w, h)
+            for d, (w, h) in zip(rng.normal(size=(n_views, 3)), sizes)]
     for persistent in (0, 1):
-        cfg = api.GESConfig(sh_degree=2, persistent=persistent)
+        cfg = api.GESConfig(sh_degree=sh_degree, persistent=persistent)
         rast, t = H.gpu_forward(sc, cams, cfg)
         ups = H.upstream(rast, 5)
         gb = rast.backward(*t, *ups)
