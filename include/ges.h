@@ -267,6 +267,29 @@ typedef struct ges_layout {
 GES_API ges_status ges_get_layout(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
                           uint64_t capacity, ges_layout *out);
 
+/* ---------------------------------------------------------------- loss
+ * Reconstruction loss of Eq. 8 (Sec. 3.2), L_rgb = (1 - lambda) L_1 + lambda L_SSIM,
+ * per view, and its gradient with respect to the rendered colour, which is the
+ * g_color that ges_render_bwd takes. Readings (the paper names the terms only):
+ * L_1 = mean over pixels and the 3 channels of |C - C_target|; L_SSIM = 1 - mean
+ * over pixels and channels of the SSIM map of Wang et al. (2004) with an 11 x 11
+ * Gaussian window of standard deviation 1.5 (normalised), C1 = 0.01^2, C2 = 0.03^2,
+ * both images taken as 0 outside the frame (zero padding), the map evaluated at
+ * every pixel. Each view has its own loss; dL_rgb(v)/dC_v is that view's gradient.
+ *
+ * Workspace: ges_loss_workspace_bytes(n_views, cams) bytes of device memory (per-CTA
+ * partial sums; contents need not be initialised; not shared by concurrent calls).
+ *   color, target  [3 * sum_v W_v H_v] planar per view, the layout of ges_render_fwd's
+ *                  color (target values are taken as given; no clamping)
+ *   lambda         weight of L_SSIM, in [0, 1] (the paper: 0.2)
+ *   loss           [n_views] float32, L_rgb of each view (written)
+ *   g_color        [like color] float32, dL_rgb(v)/dC (written); NULL: loss only
+ * The sums are formed in a fixed order (no atomics), so results are reproducible. */
+GES_API size_t ges_loss_workspace_bytes(int32_t n_views, const ges_camera *cams);
+GES_API ges_status ges_loss_rgb(int32_t n_views, const ges_camera *cams, const float *color, const float *target,
+                                float lambda, void *workspace, size_t workspace_bytes, float *loss, float *g_color,
+                                void *stream);
+
 /* Synchronises `stream`, reads and clears the device error word in `proj`, and
  * returns the first recorded condition (GES_OK if none). */
 GES_API ges_status ges_sync_status(void *proj, size_t proj_bytes, void *stream);

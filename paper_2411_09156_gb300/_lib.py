@@ -70,6 +70,8 @@ SIGNATURES = {
     "ges_sync_status": (ctypes.c_int, [_P, _S, _P]),
     "ges_render_bwd_noalloc": (ctypes.c_int, [_I, _I, _CAM, _CFG, _P, _P, _P, _P, _P, _S, _P, _S, _P, _P, _P, _P,
                                               _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ges_loss_workspace_bytes": (_S, [_I, _CAM]),
+    "ges_loss_rgb": (ctypes.c_int, [_I, _CAM, _P, _P, ctypes.c_float, _P, _S, _P, _P, _P]),
 }
 
 _lock = threading.Lock()

@@ -172,6 +172,38 @@ def ges_render_bwd_noalloc(n, n_views, cams_c, cfg_c, pos_op, lscale_beta, quat,
                                             _ptr(g_color_in), _stream(stream)), "ges_render_bwd_noalloc")
 
 
+def ges_loss_workspace_bytes(n_views, cams_c) -> int:
+    """Device bytes of the workspace ges_loss_rgb needs for these view sizes."""
+    nb = int(_lib.lib().ges_loss_workspace_bytes(n_views, cams_c))
+    if nb == 0:
+        raise ValueError("invalid views for ges_loss_rgb")
+    return nb
+
+
+def ges_loss_rgb(n_views, cams_c, color, target, lam, workspace, loss, g_color=None, stream=None) -> None:
+    """L_rgb = (1 - lam) L1 + lam (1 - SSIM) per view (Eq. 8) into loss[n_views], and its gradient
+    with respect to color into g_color (same layout as color; None: loss only)."""
+    check(_lib.lib().ges_loss_rgb(n_views, cams_c, _ptr(color), _ptr(target), float(lam), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _ptr(loss), _ptr(g_color),
+                                  _stream(stream)), "ges_loss_rgb")
+
+
+def loss_rgb(color: torch.Tensor, target: torch.Tensor, sizes: Sequence, lam: float = 0.2, stream=None):
+    """Eq. 8 loss of rendered views against targets (planar colour layout, views concatenated).
+    sizes: [(W, H)] per view. Returns (loss [n_views] float32, g_color like color)."""
+    cams = [dict(width=int(w), height=int(h), fx=1.0, fy=1.0, cx=0.0, cy=0.0,
+                 viewmat=[1.0, 0, 0, 0, 0, 1.0, 0, 0, 0, 0, 1.0, 0]) for (w, h) in sizes]
+    cams_c = cameras_to_c(cams)
+    n_px = sum(int(w) * int(h) for (w, h) in sizes)
+    if color.numel() != 3 * n_px or target.numel() != 3 * n_px:
+        raise ValueError("color and target must hold 3 * sum(W * H) values")
+    ws = torch.empty(ges_loss_workspace_bytes(len(sizes), cams_c), dtype=torch.uint8, device=color.device)
+    loss = torch.empty(len(sizes), dtype=torch.float32, device=color.device)
+    g = torch.empty_like(color)
+    ges_loss_rgb(len(sizes), cams_c, color, target, lam, ws, loss, g, stream)
+    return loss, g
+
+
 def ges_sync_status(proj, stream=None) -> int:
     """Synchronises the stream; returns (and clears) the device-recorded status code."""
     return int(_lib.lib().ges_sync_status(_ptr(proj), proj.numel(), _stream(stream)))

@@ -113,3 +113,19 @@ def test_invalid_arguments_are_rejected_on_the_host():
 def test_drt_sizes_agree_with_oracle_schedule():
     for (w, h, v) in ((1600, 1040, 8), (1920, 1080, 16), (800, 600, 3), (64, 48, 1)):
         assert drt_sizes(w, h, v) == (ODRT.batch_sizes(w, h, v) if v > 1 else [(w, h)])
+
+
+def test_loss_sizes_and_arguments_on_the_host():
+    lib = _lib.lib()
+    cams = _cams([(64, 64), (33, 31)])
+    # one CTA per 32 x 32 tile, two doubles each: 4 + 2 tiles
+    assert lib.ges_loss_workspace_bytes(2, cams) == 16 * (4 + 2)
+    assert lib.ges_loss_workspace_bytes(0, cams) == 0
+    assert lib.ges_loss_workspace_bytes(2, _cams([(64, 64), (0, 5)])) == 0
+    ws = lib.ges_loss_workspace_bytes(2, cams)
+    # null images, lambda outside [0, 1], short or misaligned workspace: rejected before any launch
+    assert lib.ges_loss_rgb(2, cams, None, 256, 0.2, 512, ws, 1024, None, None) == _lib.GES_ERR_INVALID_ARG
+    assert lib.ges_loss_rgb(2, cams, 256, 256, -0.1, 512, ws, 1024, None, None) == _lib.GES_ERR_INVALID_ARG
+    assert lib.ges_loss_rgb(2, cams, 256, 256, 0.2, 512, ws - 1, 1024, None, None) == _lib.GES_ERR_INVALID_ARG
+    assert lib.ges_loss_rgb(2, cams, 256, 256, 0.2, 516, ws, 1024, None, None) == _lib.GES_ERR_INVALID_ARG
+    assert lib.ges_loss_rgb(2, cams, 256, 256, 0.2, 512, ws, None, None, None) == _lib.GES_ERR_INVALID_ARG
