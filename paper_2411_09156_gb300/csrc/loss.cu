@@ -225,17 +225,27 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const LossArgs a) {
     }
 }
 
-// Per view: the CTA partial sums in block order, then L_rgb.
-__global__ void k_loss_finalize(const LossArgs a) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= a.n_views) return;
+// Per view (one CTA each): the CTA partial sums, thread t taking blocks t, t + 256, ...,
+// then a fixed tree over the threads; the order never depends on timing.
+__global__ void __launch_bounds__(256) k_loss_finalize(const LossArgs a) {
+    __shared__ double s0[256], s1[256];
+    const int v = blockIdx.x, t = threadIdx.x;
     double l1 = 0.0, ss = 0.0;
-    for (int b = a.block_base[v]; b < a.block_base[v + 1]; ++b) {
+    for (int b = a.block_base[v] + t; b < a.block_base[v + 1]; b += 256) {
         l1 += a.partial[2 * (size_t)b];
         ss += a.partial[2 * (size_t)b + 1];
     }
-    const double n = 3.0 * (double)a.width[v] * (double)a.height[v];
-    a.loss[v] = (float)((1.0 - (double)a.lambda) * l1 / n + (double)a.lambda * (1.0 - ss / n));
+    s0[t] = l1;
+    s1[t] = ss;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (t < o) { s0[t] += s0[t + o]; s1[t] += s1[t + o]; }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double n = 3.0 * (double)a.width[v] * (double)a.height[v];
+        a.loss[v] = (float)((1.0 - (double)a.lambda) * s0[0] / n + (double)a.lambda * (1.0 - s1[0] / n));
+    }
 }
 
 bool loss_views_ok(int32_t n_views, const ges_camera *cams) {
@@ -308,6 +318,6 @@ extern "C" ges_status ges_loss_rgb(int32_t n_views, const ges_camera *cams, cons
     if (cudaFuncSetAttribute(k_loss, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLossSmem) != cudaSuccess)
         return GES_ERR_CUDA;
     k_loss<<<nb, kLossThreads, kLossSmem, s>>>(a);
-    k_loss_finalize<<<(n_views + 31) / 32, 32, 0, s>>>(a);
+    k_loss_finalize<<<n_views, 256, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? GES_OK : GES_ERR_CUDA;
 }
