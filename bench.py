@@ -38,6 +38,8 @@ METRIC = "fwd+bwd Mpixel/s at 1.5M splats, batched vs per-view, and % of HBM roo
 F_TEST = 10          # FP32 flops per evaluated (pixel, list entry) pair: dx, dy, Q
 F_BLEND_FWD = 26     # per blended pair in the forward (falloff, alpha, transmittance, 7 accumulations)
 F_BLEND_BWD = 104    # per blended pair in the backward replay (forward blend + 78 gradient flops)
+F_LOSS = 1188        # per pixel of the Eq. 8 loss and its gradient (3 channels x 396: 5 window maps x 2
+                     # separable passes x 11 taps x 2, 3 derivative maps likewise, products, SSIM terms)
 
 
 def parse_args():
@@ -53,6 +55,7 @@ def parse_args():
     p.add_argument("--tile", default=None, help="fix the tile shape, WxH (skips the autotuner)")
     p.add_argument("--batch", type=int, default=None, help="fix the prefetch distance (skips the autotuner)")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-train-step", action="store_true", help="skip the step with the Eq. 8 loss")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the oracle sample")
     p.add_argument("--splats", type=int, default=None,
                    help="override the workload's splat count (smaller cases for profiling; not a bench line)")
@@ -421,6 +424,49 @@ def main():
         e2e = {"value": world * P / (em / 1e3) / 1e6, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": em}
 
+    # training step: the same views with the Eq. 8 loss against target images between the render
+    # passes (colour gradient from the loss instead of random upstream gradients)
+    train = None
+    if not args.no_train_step:
+        tgt_in = list(inputs)
+        gen = torch.Generator(device="cuda").manual_seed(2000 + rank)
+        tgt_in[3] = inputs[3] + 0.05 * torch.randn(inputs[3].shape, generator=gen, device="cuda")
+        tr = api.Rasterizer(sc.n, cams, cfg, capacity=plan.capacity)
+        tr.preprocess(*tgt_in)
+        tr.bin()
+        target = tr.render_fwd()["color"].clone()
+        del tr
+        tplan = BatchPlan(sc.n, cams, cfg, inputs, target=target, capacity=plan.capacity)
+        for _ in range(args.warmup):
+            tplan.step()
+        torch.cuda.synchronize()
+        tplan.check()
+        ns = len(tplan.stages)
+        tevs = [[torch.cuda.Event(enable_timing=True) for _ in range(ns + 1)] for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            tplan.step(tevs[k])
+        torch.cuda.synchronize()
+        if tplan.rast.sync_status() != 0:
+            raise RuntimeError("device status after the training steps")
+        t_stage = [statistics.mean(tevs[k][i].elapsed_time(tevs[k][i + 1]) for k in range(args.steps))
+                   for i in range(ns)]
+        t_ms = max_over_ranks(statistics.mean(tevs[k][0].elapsed_time(tevs[k][ns]) for k in range(args.steps)),
+                              world)
+        loss_ms = t_stage[tplan.stages.index("loss")]
+        loss_fl = F_LOSS * P
+        train = {"value": world * P / (t_ms / 1e3) / 1e6, "unit": "Mpixel/s", "ms_per_step": t_ms,
+                 "stages_ms": dict(zip(tplan.stages, t_stage)),
+                 "loss_per_view": [round(float(x), 6) for x in tplan.loss.cpu().tolist()],
+                 "target": "the same views rendered with SH coefficients perturbed by N(0, 0.05^2)",
+                 "loss_roofline": {"bound": "alu", "kernel": "k_loss", "achieved": loss_fl / (loss_ms / 1e3) / 1e12,
+                                   "peak": fp32_peak, "unit": "TFLOP/s",
+                                   "frac": loss_fl / (loss_ms / 1e3) / 1e12 / fp32_peak,
+                                   "flops_per_launch": loss_fl},
+                 "gpu_launches": tplan.launches_per_step() * args.steps}
+        del tplan
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, npx, secs, cores = cpu_baseline(sc, cams, cfg, args.cpu_seconds)
@@ -443,6 +489,7 @@ def main():
             "roofline": roofline,
             "per_view": per_view,
             "e2e": e2e,
+            "train_step": train,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": plan.launches_per_step() * args.steps,

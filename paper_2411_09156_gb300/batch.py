@@ -1,11 +1,14 @@
 """Batched dynamic-resolution steps as CUDA graphs, and the tile/batch autotuner.
 
 A DRT step (Eq. 15, Sec. 3.4) renders several views of uneven size forward and
-backward. BatchPlan runs it as four captured CUDA graphs -- (preprocess + bin),
+backward. BatchPlan runs it as captured CUDA graphs -- (preprocess + bin),
 render forward, render backward (screen space), preprocess backward -- over
-buffers sized for a fixed tile-instance capacity, so a step is four graph
-launches with no host synchronisation. After a replay, `check()` reads the
-device error word; a capacity overflow re-sizes the buffers and re-captures.
+buffers sized for a fixed tile-instance capacity, so a step is a few graph
+launches with no host synchronisation. With target images the step also runs
+the Eq. 8 loss between the render passes, and the render backward takes its
+colour gradient from it (a training step); otherwise it takes the given
+upstream gradients. After a replay, `check()` reads the device error word; a
+capacity overflow re-sizes the buffers and re-captures.
 """
 from __future__ import annotations
 
@@ -18,19 +21,27 @@ from typing import Dict, List, Optional, Sequence
 import torch
 
 from . import build as _build
-from .api import GESConfig, Rasterizer
+from .api import GESConfig, Rasterizer, ges_loss_rgb, ges_loss_workspace_bytes
 from ._lib import GES_ERR_CAPACITY, GES_OK, GESError
 
 STAGES = ("preprocess_bin", "render_fwd", "render_bwd", "preprocess_bwd")
+STAGES_WITH_LOSS = ("preprocess_bin", "render_fwd", "loss", "render_bwd", "preprocess_bwd")
 
 
 class BatchPlan:
     def __init__(self, n: int, cams: Sequence, cfg: GESConfig, inputs: Sequence[torch.Tensor],
-                 upstream: Sequence[Optional[torch.Tensor]], capacity: Optional[int] = None, headroom: float = 1.15,
-                 use_graphs: bool = True):
+                 upstream: Optional[Sequence[Optional[torch.Tensor]]] = None, capacity: Optional[int] = None,
+                 headroom: float = 1.15, use_graphs: bool = True, target: Optional[torch.Tensor] = None,
+                 lam: float = 0.2):
+        """upstream: (g_color, g_depth, g_alpha, g_normal) for the render backward; or target: the
+        views' target images (colour layout), whose Eq. 8 loss (weight lam on D-SSIM) supplies g_color."""
         self.n, self.cams, self.cfg = n, list(cams), cfg
         self.inputs = list(inputs)
-        self.upstream = list(upstream)
+        if (upstream is None) == (target is None):
+            raise ValueError("give either upstream gradients or target images")
+        self.target, self.lam = target, float(lam)
+        self.upstream = list(upstream) if upstream is not None else None
+        self.stages = STAGES if target is None else STAGES_WITH_LOSS
         self.headroom = headroom
         self.use_graphs = use_graphs
         if capacity is None:
@@ -45,18 +56,31 @@ class BatchPlan:
         self.capacity = capacity
         self.grads = {k: torch.empty_like(t) for k, t in
                       zip(("g_pos_op", "g_lscale_beta", "g_quat", "g_color"), self.inputs)}
-        self.graphs: List[Optional[torch.cuda.CUDAGraph]] = [None] * 4
+        if self.target is not None:
+            r = self.rast
+            if self.target.numel() != 3 * r.P:
+                raise ValueError("target must hold 3 * sum(W * H) values")
+            self.loss = torch.empty(r.n_views, dtype=torch.float32, device=r.device)
+            self.g_color_loss = torch.empty(3 * r.P, dtype=torch.float32, device=r.device)
+            self.loss_ws = torch.empty(ges_loss_workspace_bytes(r.n_views, r.cams_c), dtype=torch.uint8,
+                                       device=r.device)
+            self.upstream = [self.g_color_loss, None, None, None]
+        self.graphs: List[Optional[torch.cuda.CUDAGraph]] = [None] * len(self.stages)
         if self.use_graphs:
             self._capture()
 
     def _run_stage(self, k: int) -> None:
         r, x = self.rast, self.inputs
-        if k == 0:
+        name = self.stages[k]
+        if name == "preprocess_bin":
             r.preprocess(*x)
             r.bin()
-        elif k == 1:
+        elif name == "render_fwd":
             r.render_fwd()
-        elif k == 2:
+        elif name == "loss":
+            ges_loss_rgb(r.n_views, r.cams_c, r.out["color"], self.target, self.lam, self.loss_ws, self.loss,
+                         self.g_color_loss)
+        elif name == "render_bwd":
             r.backward_screen(*self.upstream)
         else:
             r.preprocess_bwd(*x, self.grads)
@@ -65,11 +89,11 @@ class BatchPlan:
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
-            for k in range(4):  # one eager pass before capture
+            for k in range(len(self.stages)):  # one eager pass before capture
                 self._run_stage(k)
         torch.cuda.current_stream().wait_stream(s)
         torch.cuda.synchronize()
-        for k in range(4):
+        for k in range(len(self.stages)):
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g):
                 self._run_stage(k)
@@ -83,13 +107,14 @@ class BatchPlan:
             self._run_stage(k)
 
     def step(self, events: Optional[List[torch.cuda.Event]] = None) -> Dict[str, torch.Tensor]:
-        """One fwd+bwd step; events (5, optional) bracket the four stages on the current stream."""
-        for k in range(4):
+        """One fwd+bwd step; events (len(stages) + 1, optional) bracket the stages on the current stream."""
+        n = len(self.stages)
+        for k in range(n):
             if events is not None:
                 events[k].record()
             self.run_stage(k)
         if events is not None:
-            events[4].record()
+            events[n].record()
         return self.grads
 
     def check(self) -> int:
@@ -113,7 +138,7 @@ class BatchPlan:
             binning = 1 if self.cfg.persistent else 0
         else:
             binning = 1 + 4 * 5 + 1 + 3 + 1 + 1 + tile_passes * 5 + 1 + (1 if self.cfg.persistent else 0)
-        return 1 + binning + 1 + 1 + 1
+        return 1 + binning + 1 + 1 + 1 + (2 if self.target is not None else 0)
 
 
 # --------------------------------------------------------------------------- autotune

@@ -127,3 +127,34 @@ def test_invalid_arguments_are_rejected():
         api.ges_loss_rgb(1, cams_c, x, x, 1.5, ws, loss, None)  # lambda outside [0, 1]
     with pytest.raises(api.GESError):
         api.ges_loss_rgb(1, cams_c, x, x, 0.2, ws[:8], loss, None)  # workspace too small
+
+
+def test_training_step_with_loss_matches_direct_calls():
+    """BatchPlan with target images (graphs: preprocess + bin, render, loss, render backward,
+    preprocess backward) gives the loss and gradients of the same calls made one by one."""
+    from paper_2411_09156_gb300.batch import BatchPlan
+    from paper_2411_09156_gb300.scenes import look_at, make_scene
+    sc = make_scene(3000, 21, "heightfield", 1)
+    sizes = drt_sizes(160, 104, 3)
+    rng = np.random.default_rng(22)
+    cams = [look_at(5.0 * d / np.linalg.norm(d), (0, 0, 0), w, h) for d, (w, h) in zip(rng.normal(size=(3, 3)), sizes)]
+    cfg = api.GESConfig(sh_degree=1, persistent=1)
+    inputs = api.scene_tensors(sc)
+    pert = list(inputs)
+    pert[3] = inputs[3] + 0.1
+    tr = api.Rasterizer(sc.n, cams, cfg)
+    target = tr.forward(*pert)["color"].clone()
+    plan = BatchPlan(sc.n, cams, cfg, inputs, target=target)
+    g_plan = {k: v.clone() for k, v in plan.step().items()}
+    torch.cuda.synchronize()
+    assert plan.check() == 0
+    r = api.Rasterizer(sc.n, cams, cfg)
+    out = r.forward(*inputs)
+    loss, gc = api.loss_rgb(out["color"], target, sizes, 0.2)
+    g_direct = r.backward(*inputs, gc)
+    torch.cuda.synchronize()
+    assert torch.equal(loss, plan.loss)
+    assert torch.equal(gc, plan.g_color_loss)
+    for k in g_plan:
+        rel = float((g_plan[k] - g_direct[k]).norm() / g_direct[k].norm())
+        assert rel < 1e-5, (k, rel)
