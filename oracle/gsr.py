@@ -18,7 +18,8 @@ Per sample point k (readings marked R; the paper gives the equations only):
   * Eq. 9: d(x) = sum_i o_i exp(-1/2 Q_i^(beta_i/2)), Q_i = (x - mu_i)^T Sigma_i^-1 (x - mu_i),
     Sigma_i = R_i diag(s'_i^2) R_i^T.
   * R: g* = the neighbour with the largest falloff exp(-1/2 Q_i^(beta_i/2)) (the ideal
-    scene has opacity 1), ties to the earlier neighbour.
+    scene has opacity 1), i.e. the smallest exponent Q_i^(beta_i/2); ties to the earlier
+    neighbour.
   * R: n* = the axis of g*'s smallest scale, turned so that e = <x - mu*, n*> >= 0;
     s_min = g*'s smallest phi-modulated scale.
   * Eq. 10 (exponent placement garbled in the paper), R: the ideal density is a flat
@@ -26,7 +27,9 @@ Per sample point k (readings marked R; the paper gives the equations only):
   * Eq. 11, R: f = s_min sqrt(-2 ln d), fbar = s_min sqrt(-2 ln dbar) (the "+" branch),
     with d clamped to [1e-30, 1] (a sum of overlapping splats can exceed 1).
   * Eq. 12: L_sdf = mean_k |fbar - f|.
-  * Eq. 13: L_nor = mean_k || grad f / |grad f| - n* ||^2, grad f taken in x.
+  * Eq. 13: L_nor = mean_k || grad f / |grad f| - n* ||^2, grad f taken in x (its
+    direction, that of -grad d, from the sum of the neighbours' terms scaled by the
+    largest one, so it stays defined where d underflows).
   * The value returned for the step is lambda_sdf L_sdf + lambda_nor L_nor (the
     weights of Eq. 14 are not given in the paper and are the caller's).
 
@@ -81,12 +84,12 @@ def knn_distances(pos: np.ndarray, idx: np.ndarray) -> np.ndarray:
 
 
 def evaluate(pos_op, lscale_beta, quat, knn_idx, sample_splat, sample_z, rho=0.1, phi_mode=1,
-             lambda_sdf=1.0, lambda_nor=1.0, with_grad=True, flag_eps=1e-5):
+             lambda_sdf=1.0, lambda_nor=1.0, with_grad=True, flag_eps=1e-4):
     """GSR losses at the sample points and their gradient with respect to the splat parameters.
 
     Returns dict(l_sdf, l_nor, loss, x (M,3), d, f, fbar, cos (u . n*), gstar (M,) neighbour
-    slot of g*, flags (M,) bool: g* decided by a relative falloff gap below flag_eps or e
-    within flag_eps of 0, grads dict g_pos_op, g_lscale_beta, g_quat (N,4) or None)."""
+    slot of g*, flags (M,) bool: g* decided by an exponent gap below flag_eps (1 + P) or e
+    within flag_eps s_min of 0, grads dict g_pos_op, g_lscale_beta, g_quat (N,4) or None)."""
     po = torch.tensor(np.asarray(pos_op, np.float64), requires_grad=with_grad)
     lsb = torch.tensor(np.asarray(lscale_beta, np.float64), requires_grad=with_grad)
     qt = torch.tensor(np.asarray(quat, np.float64), requires_grad=with_grad)
@@ -108,11 +111,15 @@ def evaluate(pos_op, lscale_beta, quat, knn_idx, sample_splat, sample_z, rho=0.1
     G = torch.exp(-0.5 * Q ** hb)
     t = op[ni] * G
     d = t.sum(-1)
-    # g*: largest falloff, first on ties
-    Gd = G.detach()
-    gslot = torch.argmax(Gd, dim=1)  # torch returns the first maximal index
-    top2 = torch.topk(Gd, 2, dim=1).values
-    flags = (top2[:, 0] - top2[:, 1]) <= flag_eps * top2[:, 0]
+    # g*: largest falloff, first on ties -- the smallest exponent P = Q^(beta/2), since
+    # G = exp(-P/2) decreases in P; P does not underflow where G does
+    P = Q ** hb
+    Pd = P.detach()
+    gslot = torch.argmin(Pd, dim=1)  # torch returns the first minimal index
+    # a near tie: float32 evaluates P with an error relative to P, so exponents within
+    # flag_eps (1 + P) of each other may swap order
+    low2 = torch.topk(Pd, 2, dim=1, largest=False).values
+    flags = (low2[:, 1] - low2[:, 0]) <= flag_eps * (1.0 + low2[:, 0])
     gs = ni[torch.arange(ni.shape[0]), gslot]
     kmin = torch.argmin(lsb.detach()[:, :3], dim=1)  # smallest scale axis (ties: lowest index)
     n_raw = R[gs, :, kmin[gs]]  # (M, 3) column kmin of R*
@@ -128,16 +135,15 @@ def evaluate(pos_op, lscale_beta, quat, knn_idx, sample_splat, sample_z, rho=0.1
     pl = -2.0 * torch.log(dc)
     pos = pl > 0
     f = torch.where(pos, smin * torch.sqrt(torch.where(pos, pl, torch.ones_like(pl))), torch.zeros_like(pl))
-    # grad f in x: -s_min^2 grad d / (d f); its direction is that of w = -grad d
-    gd = torch.autograd.grad(d.sum(), x, create_graph=with_grad)[0] if with_grad else None
-    if gd is None:
-        with torch.enable_grad():
-            xg = x.detach().requires_grad_(True)
-            dl = xg[:, None, :] - mu.detach()[ni]
-            lc = torch.einsum("mkab,mka->mkb", R.detach()[ni], dl) / sp.detach()[ni]
-            dd = (op.detach()[ni] * torch.exp(-0.5 * ((lc * lc).sum(-1)) ** hb.detach())).sum(-1)
-            gd = torch.autograd.grad(dd.sum(), xg)[0]
-    w = -gd
+    # grad f in x is -s_min^2 grad d / (d f): its direction is that of
+    # -grad d = sum_i t_i (beta_i/2) Q_i^(beta_i/2 - 1) Sigma_i^-1 (x - mu_i). A positive
+    # common factor does not change the direction, so the sum is taken relative to the
+    # largest term, exp(-P_min/2), which keeps it representable when every t_i underflows
+    # (samples far out in the tail of all 16 neighbours).
+    pmin = Pd.min(dim=1, keepdim=True).values
+    rel = op[ni] * torch.exp(-0.5 * (P - pmin)) * hb * P / Q  # t_i (beta_i/2) Q^(beta_i/2-1) / exp(-P_min/2)
+    ainv = torch.einsum("mkab,mkb->mka", R[ni], loc / sp[ni])  # Sigma_i^-1 (x - mu_i) = R diag(1/s') loc
+    w = (rel[..., None] * ainv).sum(1)
     u = w / torch.linalg.norm(w, dim=-1, keepdim=True)
     cosv = (u * nstar).sum(-1)
     l_sdf = (fbar - f).abs().mean()

@@ -125,3 +125,54 @@ def test_gradient_matches_central_differences(phi_mode):
                              lambda_sdf=1.0, lambda_nor=0.5, with_grad=False)["loss"]
             fd = (lp - lm) / (2 * h)
             assert abs(fd - g[i, c]) <= 1e-6 * max(1.0, abs(fd)), (name, i, c, fd, g[i, c])
+
+
+def test_normal_direction_is_minus_the_density_gradient():
+    # the explicit direction sum against autograd of the density itself, where nothing underflows
+    n = 80
+    pos, lsb, q = _scene(n, 8)
+    lsb[:, :3] += 1.0  # wide splats: every sample sees several neighbours
+    knn = OG.knn(pos)
+    rng = np.random.default_rng(9)
+    js, z = rng.integers(0, n, 30), 0.5 * rng.normal(size=(30, 3))
+    out = OG.evaluate(pos, lsb, q, knn, js, z, with_grad=False)
+    po, ls, qt = (torch.tensor(a, dtype=torch.float64) for a in (pos, lsb, q))
+    R = OG.rotation(qt)
+    sp = OG.phi(ls[:, 3], 0.1, 1)[:, None] * torch.exp(ls[:, :3])
+    for k in range(30):
+        x = torch.tensor(out["x"][k], requires_grad=True)
+        d = 0.0
+        for i in knn[js[k]]:
+            loc = (R[i].T @ (x - po[i, :3])) / sp[i]
+            d = d + po[i, 3] * torch.exp(-0.5 * (loc @ loc) ** (ls[i, 3] / 2))
+        (gd,) = torch.autograd.grad(d, x)
+        u = -gd / torch.linalg.norm(gd)
+        g = int(knn[js[k]][out["gstar"][k]])
+        nrm = R[g][:, int(torch.argmin(ls[g, :3]))]
+        nrm = nrm * torch.sign(nrm @ (x.detach() - po[g, :3]))
+        assert abs(float(u @ nrm) - out["cos"][k]) < 1e-10
+
+
+def test_far_sample_with_underflowing_density_keeps_a_defined_normal():
+    # |z|^2 = 200 and beta = 6: the density is exp(-4e6), zero in any float format, yet the
+    # direction of -grad d is that of the splat's own term
+    n = 16
+    pos = np.zeros((n, 4))
+    pos[1:, :3] = 50.0 + np.arange(15)[:, None]
+    pos[0, 3] = 0.9
+    lsb = np.zeros((n, 4))
+    lsb[:, :3] = [np.log(0.3), np.log(0.2), np.log(0.05)]
+    lsb[:, 3] = 6.0
+    qv = np.array([0.9, 0.2, -0.3, 0.1])
+    q = np.tile(qv, (n, 1))
+    knn = np.tile(np.arange(n), (n, 1))
+    z = np.array([[10.0, -6.0, 7.48331477]])
+    out = OG.evaluate(pos, lsb, q, knn, [0], z, with_grad=False)
+    assert out["d"][0] == 0.0 and np.isfinite(out["f"][0]) and np.isfinite(out["l_nor"])
+    R = Rotation.from_quat(qv[[1, 2, 3, 0]]).as_matrix()
+    s = np.exp(lsb[0, :3]) * 2 / (1 + np.exp(-0.1 * 4.0))
+    x = R @ (s * z[0])
+    A = R @ np.diag(1 / s ** 2) @ R.T
+    u = A @ x / np.linalg.norm(A @ x)
+    nrm = R[:, 2] * np.sign(R[:, 2] @ x)
+    np.testing.assert_allclose(out["cos"][0], u @ nrm, rtol=0, atol=1e-12)
