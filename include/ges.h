@@ -286,6 +286,60 @@ GES_API ges_status ges_get_layout(int32_t n, int32_t n_views, const ges_camera *
  *   g_color        [like color] float32, dL_rgb(v)/dC (written); NULL: loss only
  * The sums are formed in a fixed order (no atomics), so results are reproducible. */
 GES_API size_t ges_loss_workspace_bytes(int32_t n_views, const ges_camera *cams);
+
+/* ---------------------------------------------------------------- KNN (GSR neighbours)
+ * The GES_KNN_K = 16 splat centres nearest to each splat centre (Euclidean, the
+ * splat itself included), for the density of the generalized surface regularization
+ * (Sec. 3.3, Eq. 9; the paper sums over the 16 closest points, Sec. 4.2).
+ *   pos_op   [n, 4] float32 (x, y, z, opacity), 16-byte aligned; opacity unused
+ *   knn      [n, 16] int32 (written): splat i's neighbours by increasing distance,
+ *            ties to the lower index (so neighbour 0 is i itself unless another centre
+ *            coincides with it and has a lower index)
+ * Exact (distances are squared float32 differences summed in x, y, z order) unless
+ * one query must examine more than 65,536 candidate centres (tens of thousands of
+ * coincident centres, or non-finite coordinates); its list is then the best among
+ * those examined. Workspace: ges_knn_workspace_bytes(n) bytes, 256-byte aligned, no
+ * initialisation needed. n must be in [16, 2^26]; otherwise both calls reject it
+ * (0 / GES_ERR_INVALID_ARG). */
+#define GES_KNN_K 16
+GES_API size_t ges_knn_workspace_bytes(int32_t n);
+GES_API ges_status ges_knn(int32_t n, const float *pos_op, void *workspace, size_t workspace_bytes, int32_t *knn,
+                           void *stream);
+
+/* ---------------------------------------------------------------- GSR point evaluation
+ * Generalized surface regularization at m sample points (Sec. 3.3): the density of
+ * Eq. 9 over the GES_KNN_K splats nearest to the splat a sample was drawn from, the
+ * ideal flat density of Eq. 10, the SDFs of Eq. 11, L_sdf (Eq. 12), L_nor (Eq. 13),
+ * and the gradient of lambda_sdf L_sdf + lambda_nor L_nor (the weights of Eq. 14 are
+ * the caller's; the paper does not give them). Readings (the paper gives the
+ * equations only):
+ *  - sample k is x = mu_j + R_j (s'_j * z_k), j = sample_splat[k], z_k ~ N(0, I) given
+ *    (sample_z [m, 3]); gradients flow through x to splat j;
+ *  - its neighbours are knn[j] (ges_knn: the 16 centres nearest to splat j, j included);
+ *  - d = sum_i o_i exp(-1/2 P_i), P_i = Q_i^(beta_i/2), Q_i the Mahalanobis distance
+ *    under Sigma_i = R_i diag(s'_i^2) R_i^T, s' = phi(beta) exp(l) (cfg->phi_mode and
+ *    cfg->rho as in the rasterizer; the other fields of cfg are not used);
+ *  - g* = the neighbour with the largest exp(-1/2 P_i), i.e. the smallest P_i (ties: the
+ *    earlier one); n* = g*'s smallest-scale axis turned so that e = <x - mu*, n*> >= 0;
+ *    s_min = g*'s smallest s'; ideal density dbar = exp(-1/2 (e^2 / s_min^2)^(beta* / 2));
+ *  - f = s_min sqrt(-2 ln d) with d clamped to [1e-30, 1], fbar = s_min sqrt(-2 ln dbar);
+ *  - L_sdf = mean |fbar - f|; L_nor = mean |u - n*|^2 with u the direction of grad f,
+ *    i.e. of -grad d, summed relative to its largest term so that it stays defined
+ *    where d underflows.
+ * Inputs as for ges_preprocess; knn [n, 16] int32 (entries outside [0, n) are skipped);
+ * sample_splat [m] int32 (samples outside [0, n) contribute nothing, but count in m).
+ * Outputs: losses [3] float32 (L_sdf, L_nor, lambda_sdf L_sdf + lambda_nor L_nor);
+ * sample_out [m, 8] float32 or NULL: x, y, z, d, f, fbar, u . n*, g*'s neighbour slot;
+ * g_pos_op, g_lscale_beta, g_quat [n, 4] float32 (written, not accumulated), or all
+ * three NULL for the losses only. Workspace: ges_gsr_workspace_bytes(n, m) bytes,
+ * 256-byte aligned, no initialisation needed. Gradient sums use float atomics, so
+ * their last bits vary from run to run; the losses are summed in a fixed order. */
+GES_API size_t ges_gsr_workspace_bytes(int32_t n, int32_t m);
+GES_API ges_status ges_gsr(int32_t n, const float *pos_op, const float *lscale_beta, const float *quat,
+                           const ges_config *cfg, const int32_t *knn, int32_t m, const int32_t *sample_splat,
+                           const float *sample_z, float lambda_sdf, float lambda_nor, void *workspace,
+                           size_t workspace_bytes, float *losses, float *sample_out, float *g_pos_op,
+                           float *g_lscale_beta, float *g_quat, void *stream);
 GES_API ges_status ges_loss_rgb(int32_t n_views, const ges_camera *cams, const float *color, const float *target,
                                 float lambda, void *workspace, size_t workspace_bytes, float *loss, float *g_color,
                                 void *stream);

@@ -87,9 +87,13 @@ def evaluate(pos_op, lscale_beta, quat, knn_idx, sample_splat, sample_z, rho=0.1
              lambda_sdf=1.0, lambda_nor=1.0, with_grad=True, flag_eps=1e-4):
     """GSR losses at the sample points and their gradient with respect to the splat parameters.
 
-    Returns dict(l_sdf, l_nor, loss, x (M,3), d, f, fbar, cos (u . n*), gstar (M,) neighbour
-    slot of g*, flags (M,) bool: g* decided by an exponent gap below flag_eps (1 + P) or e
-    within flag_eps s_min of 0, grads dict g_pos_op, g_lscale_beta, g_quat (N,4) or None)."""
+    Returns dict(l_sdf, l_nor, loss, x (M,3), d, f, fbar, cos (u . n*), e, smin, beta_star,
+    wcond (the direction terms' total length over the length of their sum), pscale (the largest
+    (beta/2) Q^(beta/2) among the direction's terms above 1e-3 of the largest), gstar (M,)
+    neighbour slot of g*, flags (M,) bool: g* decided by an exponent gap below flag_eps (1 + P),
+    e within flag_eps s_min of 0, |fbar - f| within flag_eps (fbar + f), |ln d| within flag_eps,
+    d within 5 % of the lower clamp, or pscale above 60; grads dict g_pos_op, g_lscale_beta,
+    g_quat (N,4) or None)."""
     po = torch.tensor(np.asarray(pos_op, np.float64), requires_grad=with_grad)
     lsb = torch.tensor(np.asarray(lscale_beta, np.float64), requires_grad=with_grad)
     qt = torch.tensor(np.asarray(quat, np.float64), requires_grad=with_grad)
@@ -146,12 +150,29 @@ def evaluate(pos_op, lscale_beta, quat, knn_idx, sample_splat, sample_z, rho=0.1
     w = (rel[..., None] * ainv).sum(1)
     u = w / torch.linalg.norm(w, dim=-1, keepdim=True)
     cosv = (u * nstar).sum(-1)
+    # conditioning of the direction: the sum of the terms' lengths over the length of their
+    # sum, and the largest (beta/2) P among the terms that matter (float32 rounds P to about
+    # 2.5e-6 (beta/2) P, so the terms' relative weights exp(-P/2) carry half that)
+    wcond = ((rel[..., None] * ainv).norm(dim=-1).sum(1) / torch.linalg.norm(w, dim=-1)).detach()
+    live = torch.exp(-0.5 * (Pd - pmin)) >= 1e-3
+    pscale = torch.where(live, (hb * P).detach(), torch.zeros_like(Pd)).max(dim=1).values
+    # decisions float32 may take the other way: the kink of |fbar - f|, d at the clamp at 1
+    # (where f's derivative in d diverges), and samples so far in the tails that a term that
+    # matters has (beta/2) P above 60: float32 rounds P to about 2.5e-6 (beta/2) P, and the
+    # weights' derivatives carry a further factor of about P / 2, so their gradient terms are
+    # uncertain to 2.5e-6 P^2 / 2, about 5e-3 at 60
+    fd_, fbd = f.detach(), fbar.detach()
+    flags = flags | ((fbd - fd_).abs() <= flag_eps * (fbd + fd_)) | (torch.log(d.detach()).abs() <= flag_eps)
+    flags = flags | (pscale > 60.0)
+    # d at the lower clamp (1e-30), whose side decides whether the density path carries gradient
+    flags = flags | ((torch.log(d.detach().clamp(min=1e-300)) - np.log(D_MIN)).abs() <= 0.05)
     l_sdf = (fbar - f).abs().mean()
     l_nor = ((u - nstar) ** 2).sum(-1).mean()
     loss = lambda_sdf * l_sdf + lambda_nor * l_nor
     out = dict(l_sdf=float(l_sdf.detach()), l_nor=float(l_nor.detach()), loss=float(loss.detach()), x=x.detach().numpy(),
                d=d.detach().numpy(), f=f.detach().numpy(), fbar=fbar.detach().numpy(), cos=cosv.detach().numpy(),
-               gstar=gslot.numpy(), flags=flags.numpy(), grads=None)
+               e=e.detach().numpy(), smin=smin.detach().numpy(), beta_star=(2.0 * hs).detach().numpy(),
+               wcond=wcond.numpy(), pscale=pscale.numpy(), gstar=gslot.numpy(), flags=flags.numpy(), grads=None)
     if with_grad:
         g = torch.autograd.grad(loss, [po, lsb, qt], allow_unused=True)
         out["grads"] = dict(g_pos_op=g[0].numpy(), g_lscale_beta=g[1].numpy(), g_quat=g[2].numpy())

@@ -204,6 +204,62 @@ def loss_rgb(color: torch.Tensor, target: torch.Tensor, sizes: Sequence, lam: fl
     return loss, g
 
 
+def ges_knn_workspace_bytes(n: int) -> int:
+    nb = int(_lib.lib().ges_knn_workspace_bytes(n))
+    if nb == 0:
+        raise ValueError("ges_knn needs 16 <= n <= 2^26 splats")
+    return nb
+
+
+def ges_knn(n, pos_op, workspace, knn, stream=None) -> None:
+    """The 16 nearest splat centres of every splat (self included) into knn [n, 16] int32."""
+    check(_lib.lib().ges_knn(n, _ptr(pos_op), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                             _ptr(knn), _stream(stream)), "ges_knn")
+
+
+def ges_gsr_workspace_bytes(n: int, m: int) -> int:
+    nb = int(_lib.lib().ges_gsr_workspace_bytes(n, m))
+    if nb == 0:
+        raise ValueError("invalid sizes for ges_gsr")
+    return nb
+
+
+def ges_gsr(n, pos_op, lscale_beta, quat, cfg_c, knn, m, sample_splat, sample_z, lambda_sdf, lambda_nor, workspace,
+            losses, sample_out=None, g_pos_op=None, g_lscale_beta=None, g_quat=None, stream=None) -> None:
+    """GSR losses (Eq. 9-13) at m sample points into losses[3]; their gradient into g_* (or None)."""
+    check(_lib.lib().ges_gsr(n, _ptr(pos_op), _ptr(lscale_beta), _ptr(quat), ctypes.byref(cfg_c), _ptr(knn), m,
+                             _ptr(sample_splat), _ptr(sample_z), float(lambda_sdf), float(lambda_nor),
+                             _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(losses),
+                             _ptr(sample_out), _ptr(g_pos_op), _ptr(g_lscale_beta), _ptr(g_quat), _stream(stream)),
+          "ges_gsr")
+
+
+def knn(pos_op: torch.Tensor, stream=None) -> torch.Tensor:
+    """[n, 16] int32 nearest-centre lists of the splats in pos_op [n, 4]."""
+    n = pos_op.shape[0]
+    ws = torch.empty(ges_knn_workspace_bytes(n), dtype=torch.uint8, device=pos_op.device)
+    out = torch.empty((n, 16), dtype=torch.int32, device=pos_op.device)
+    ges_knn(n, pos_op, ws, out, stream)
+    return out
+
+
+def gsr(pos_op, lscale_beta, quat, knn_idx, sample_splat, sample_z, cfg: Optional["GESConfig"] = None,
+        lambda_sdf: float = 1.0, lambda_nor: float = 1.0, grads: bool = True, per_sample: bool = False,
+        stream=None) -> Dict[str, Optional[torch.Tensor]]:
+    """GSR losses at the samples and (optionally) their gradient. Returns dict(losses [3]: L_sdf, L_nor,
+    weighted sum; g_pos_op, g_lscale_beta, g_quat or None; sample_out [m, 8] or None)."""
+    cfg = cfg or GESConfig()
+    n, m = pos_op.shape[0], sample_splat.shape[0]
+    dev = pos_op.device
+    ws = torch.empty(ges_gsr_workspace_bytes(n, m), dtype=torch.uint8, device=dev)
+    losses = torch.empty(3, dtype=torch.float32, device=dev)
+    so = torch.empty((m, 8), dtype=torch.float32, device=dev) if per_sample else None
+    g = [torch.empty_like(pos_op), torch.empty_like(lscale_beta), torch.empty_like(quat)] if grads else [None] * 3
+    ges_gsr(n, pos_op, lscale_beta, quat, cfg.to_c(), knn_idx, m, sample_splat, sample_z, lambda_sdf, lambda_nor,
+            ws, losses, so, *g, stream=stream)
+    return dict(losses=losses, g_pos_op=g[0], g_lscale_beta=g[1], g_quat=g[2], sample_out=so)
+
+
 def ges_sync_status(proj, stream=None) -> int:
     """Synchronises the stream; returns (and clears) the device-recorded status code."""
     return int(_lib.lib().ges_sync_status(_ptr(proj), proj.numel(), _stream(stream)))

@@ -1,0 +1,286 @@
+// Exact k = 16 nearest splat centres (Sec. 4.2: the GSR density at a sample uses
+// the 16 splats closest to the splat it was drawn from).
+//
+// A uniform grid over the centres' bounding box, at most two cells per point, is
+// built on the device: cell keys, a stable radix sort of the points by cell (the
+// sort of the binning), dense cell ranges and a cell-ordered copy of the centres.
+// Each query then walks Chebyshev rings of cells around its own cell, keeping its 16
+// best (distance, index) pairs sorted in registers, and stops once the 16th best
+// distance is within the distance from the query to the outside of the searched
+// block (no unsearched point can be closer). Queries run in cell order, so a warp
+// searches one neighbourhood. Distances are squared float32 with a fixed operation
+// order; ties go to the lower index. A query examines at most 65,536 candidates (a
+// bound that well-spread centres never reach; tens of thousands of coincident
+// centres would), so no input makes the search quadratic.
+#include "ges_internal.cuh"
+
+namespace ges {
+
+cudaError_t radix_sort(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, const uint32_t *n_dev,
+                       uint32_t n_host_max, int bits, uint32_t *hist, uint32_t *partials, cudaStream_t s);
+
+namespace {
+
+constexpr int kK = GES_KNN_K;
+constexpr uint32_t kQueryBudget = 1u << 16;  // candidate points one query may examine
+
+struct KnnGrid {
+    float lo[3];
+    float h, inv_h;
+    int dims[3];
+};
+
+struct KnnLayout {
+    uint64_t bbox, grid, keys0, keys1, vals0, vals1, hist, partials, ranges, spos, bytes;
+    uint32_t cap_cells, nblocks;
+    int bits;
+};
+
+inline uint64_t al256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+KnnLayout knn_layout(int32_t n) {
+    KnnLayout L;
+    uint64_t cap = 2ull * (uint64_t)n;
+    if (cap < 1) cap = 1;
+    if (cap > (1ull << 27)) cap = 1ull << 27;
+    L.cap_cells = (uint32_t)cap;
+    L.bits = 1;
+    while ((1ull << L.bits) < cap) ++L.bits;
+    L.nblocks = ceil_div_u64(n > 0 ? (uint64_t)n : 1, kSortTile);
+    uint64_t off = 0;
+    L.bbox = off; off = al256(off + 6 * 4);
+    L.grid = off; off = al256(off + sizeof(KnnGrid));
+    L.keys0 = off; off = al256(off + 4ull * n);
+    L.keys1 = off; off = al256(off + 4ull * n);
+    L.vals0 = off; off = al256(off + 4ull * n);
+    L.vals1 = off; off = al256(off + 4ull * n);
+    L.hist = off; off = al256(off + 4ull * 256 * L.nblocks);
+    L.partials = off; off = al256(off + 4ull * (ceil_div_u64(256ull * L.nblocks, kScanTile) + 1));
+    L.ranges = off; off = al256(off + 8ull * L.cap_cells);
+    L.spos = off; off = al256(off + 16ull * n);
+    L.bytes = off;
+    return L;
+}
+
+// float <-> order-preserving uint32 (for atomic min / max)
+__device__ __forceinline__ uint32_t f2ord(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void __launch_bounds__(256) k_knn_bbox(const float4 *pos, int n, uint32_t *bb) {
+    uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 p = __ldg(pos + i);
+        const float c[3] = {p.x, p.y, p.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t o = f2ord(c[k]);
+            mn[k] = min(mn[k], o);
+            mx[k] = max(mx[k], o);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        mn[k] = __reduce_min_sync(0xffffffffu, mn[k]);
+        mx[k] = __reduce_max_sync(0xffffffffu, mx[k]);
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(bb + k, mn[k]);
+            atomicMax(bb + 3 + k, mx[k]);
+        }
+    }
+}
+
+// Cell size h with at most cap cells: start from the volume per cell, then grow h
+// until the product of the per-axis counts fits (flat boxes have a zero extent).
+__global__ void k_knn_grid(const uint32_t *bb, uint32_t cap, KnnGrid *g) {
+    float lo[3], ext[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = ord2f(bb[k]);
+        ext[k] = fmaxf(ord2f(bb[3 + k]) - lo[k], 0.f);
+    }
+    const float emax = fmaxf(fmaxf(ext[0], ext[1]), ext[2]);
+    float h = emax > 0.f ? emax : 1.f;
+    const double vol = (double)fmaxf(ext[0], 1e-30f) * fmaxf(ext[1], 1e-30f) * fmaxf(ext[2], 1e-30f);
+    const double h0 = cbrt(vol / (double)cap);
+    if (h0 > 0.0 && h0 < (double)h) h = (float)h0;
+    int d[3] = {1, 1, 1};
+    bool fits = false;
+    for (int it = 0; it < 256 && !fits; ++it) {
+        double prod = 1.0;
+        for (int k = 0; k < 3; ++k) {
+            d[k] = (int)fminf(fmaxf(floorf(ext[k] / h) + 1.f, 1.f), 2048.f);
+            prod *= d[k];
+        }
+        fits = prod <= (double)cap;
+        if (!fits) h *= 1.0625f;
+    }
+    if (!fits || !(h > 0.f) || !isfinite(h)) {  // non-finite coordinates: one cell (the query budget bounds the work)
+        d[0] = d[1] = d[2] = 1;
+        h = 1.f;
+    }
+    for (int k = 0; k < 3; ++k) {
+        g->lo[k] = isfinite(lo[k]) ? lo[k] : 0.f;
+        g->dims[k] = d[k];
+    }
+    g->h = h;
+    g->inv_h = 1.f / h;
+}
+
+__device__ __forceinline__ int cell_axis(float p, float lo, float inv_h, int dim) {
+    const int c = (int)floorf((p - lo) * inv_h);
+    return min(max(c, 0), dim - 1);
+}
+
+__global__ void __launch_bounds__(256) k_knn_keys(const float4 *pos, int n, const KnnGrid *g, uint32_t *keys) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 p = __ldg(pos + i);
+    const KnnGrid G = *g;
+    const int cx = cell_axis(p.x, G.lo[0], G.inv_h, G.dims[0]);
+    const int cy = cell_axis(p.y, G.lo[1], G.inv_h, G.dims[1]);
+    const int cz = cell_axis(p.z, G.lo[2], G.inv_h, G.dims[2]);
+    keys[i] = (uint32_t)(cx + G.dims[0] * (cy + G.dims[1] * cz));
+}
+
+__global__ void __launch_bounds__(256) k_knn_ranges(const uint32_t *keys, const uint32_t *idx, const float4 *pos,
+                                                    int n, uint2 *ranges, float4 *spos) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint32_t k = keys[r];
+    if (r == 0 || keys[r - 1] != k) ranges[k].x = (uint32_t)r;
+    if (r == n - 1 || keys[r + 1] != k) ranges[k].y = (uint32_t)r + 1;
+    const uint32_t i = idx[r];
+    const float4 p = __ldg(pos + i);
+    spos[r] = make_float4(p.x, p.y, p.z, __uint_as_float(i));
+}
+
+__device__ __forceinline__ float dist2(float4 a, float4 b) {
+    const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+__global__ void __launch_bounds__(128) k_knn_query(const float4 *spos, const uint2 *ranges, const KnnGrid *gp, int n,
+                                                   int32_t *knn) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const KnnGrid G = *gp;
+    const float4 p = spos[r];
+    const uint32_t self = __float_as_uint(p.w);
+    const int c[3] = {cell_axis(p.x, G.lo[0], G.inv_h, G.dims[0]), cell_axis(p.y, G.lo[1], G.inv_h, G.dims[1]),
+                      cell_axis(p.z, G.lo[2], G.inv_h, G.dims[2])};
+    const float pc[3] = {p.x, p.y, p.z};
+    float bd[kK];
+    uint32_t bi[kK];
+#pragma unroll
+    for (int k = 0; k < kK; ++k) { bd[k] = __int_as_float(0x7f800000); bi[k] = 0xffffffffu; }
+    const int rmax = max(max(G.dims[0], G.dims[1]), G.dims[2]);
+    uint32_t examined = 0;
+    for (int ring = 0; ring <= rmax && examined < kQueryBudget; ++ring) {
+        const int z0 = max(c[2] - ring, 0), z1 = min(c[2] + ring, G.dims[2] - 1);
+        const int y0 = max(c[1] - ring, 0), y1 = min(c[1] + ring, G.dims[1] - 1);
+        const int x0 = max(c[0] - ring, 0), x1 = min(c[0] + ring, G.dims[0] - 1);
+        auto visit = [&](int cx, int cy, int cz) {
+            const uint2 rg = __ldg(ranges + (cx + G.dims[0] * (cy + G.dims[1] * cz)));
+            const uint32_t end = min(rg.y, rg.x + (kQueryBudget - min(examined, kQueryBudget)));
+            examined += rg.y - rg.x;
+            for (uint32_t q = rg.x; q < end; ++q) {
+                const float4 o = __ldg(spos + q);
+                const float d = dist2(p, o);
+                uint32_t id = __float_as_uint(o.w);
+                if (d > bd[kK - 1] || (d == bd[kK - 1] && id >= bi[kK - 1])) continue;
+                float cd = d;
+#pragma unroll
+                for (int k = 0; k < kK; ++k) {  // insert, keeping (distance, index) order
+                    const bool less = cd < bd[k] || (cd == bd[k] && id < bi[k]);
+                    const float td = bd[k];
+                    const uint32_t ti = bi[k];
+                    bd[k] = less ? cd : td;
+                    bi[k] = less ? id : ti;
+                    cd = less ? td : cd;
+                    id = less ? ti : id;
+                }
+            }
+        };
+        // the cells at Chebyshev distance `ring` from the query's cell
+        for (int cz = z0; cz <= z1; ++cz) {
+            for (int cy = y0; cy <= y1; ++cy) {
+                if (abs(cz - c[2]) < ring && abs(cy - c[1]) < ring) {  // only the two x faces are new
+                    if (c[0] - ring >= 0) visit(c[0] - ring, cy, cz);
+                    if (c[0] + ring < G.dims[0]) visit(c[0] + ring, cy, cz);
+                } else {
+                    for (int cx = x0; cx <= x1; ++cx) visit(cx, cy, cz);
+                }
+            }
+        }
+        // every point outside the searched block is at least `bound` away
+        float bound = __int_as_float(0x7f800000);
+        bool all = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (c[k] - ring > 0) { bound = fminf(bound, pc[k] - (G.lo[k] + (float)(c[k] - ring) * G.h)); all = false; }
+            if (c[k] + ring < G.dims[k] - 1) {
+                bound = fminf(bound, (G.lo[k] + (float)(c[k] + ring + 1) * G.h) - pc[k]);
+                all = false;
+            }
+        }
+        if (all) break;
+        bound = fmaxf(bound, 0.f);
+        if (bi[kK - 1] != 0xffffffffu && bd[kK - 1] <= bound * bound * (1.f - 1.f / 1048576.f)) break;
+    }
+    int32_t *out = knn + (size_t)self * kK;
+#pragma unroll
+    for (int k = 0; k < kK; ++k) out[k] = (int32_t)bi[k];
+}
+
+template <class T>
+T *at(void *base, uint64_t off) {
+    return reinterpret_cast<T *>(static_cast<char *>(base) + off);
+}
+
+}  // namespace
+}  // namespace ges
+
+using namespace ges;
+
+extern "C" size_t ges_knn_workspace_bytes(int32_t n) {
+    if (n < GES_KNN_K || (uint64_t)n > (1ull << 26)) return 0;
+    return knn_layout(n).bytes;
+}
+
+extern "C" ges_status ges_knn(int32_t n, const float *pos_op, void *workspace, size_t workspace_bytes, int32_t *knn,
+                              void *stream) {
+    if (n < GES_KNN_K || (uint64_t)n > (1ull << 26) || !pos_op || !workspace || !knn) return GES_ERR_INVALID_ARG;
+    if (((uintptr_t)pos_op & 15u) || ((uintptr_t)workspace & 255u) || ((uintptr_t)knn & 3u))
+        return GES_ERR_INVALID_ARG;
+    const KnnLayout L = knn_layout(n);
+    if (workspace_bytes < L.bytes) return GES_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float4 *pos = reinterpret_cast<const float4 *>(pos_op);
+    uint32_t *bb = at<uint32_t>(workspace, L.bbox);
+    KnnGrid *grid = at<KnnGrid>(workspace, L.grid);
+    cudaError_t e = cudaMemsetAsync(bb, 0xff, 12, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bb + 3, 0, 12, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(at<void>(workspace, L.ranges), 0, 8ull * L.cap_cells, s);
+    if (e != cudaSuccess) return GES_ERR_CUDA;
+    k_knn_bbox<<<min(ceil_div_u64(n, 256), 1024u), 256, 0, s>>>(pos, n, bb);
+    k_knn_grid<<<1, 1, 0, s>>>(bb, L.cap_cells, grid);
+    uint32_t *keys[2] = {at<uint32_t>(workspace, L.keys0), at<uint32_t>(workspace, L.keys1)};
+    uint32_t *vals[2] = {at<uint32_t>(workspace, L.vals0), at<uint32_t>(workspace, L.vals1)};
+    k_knn_keys<<<ceil_div_u64(n, 256), 256, 0, s>>>(pos, n, grid, keys[0]);
+    e = radix_sort(keys, vals, true, nullptr, (uint32_t)n, L.bits, at<uint32_t>(workspace, L.hist),
+                   at<uint32_t>(workspace, L.partials), s);
+    if (e != cudaSuccess) return GES_ERR_CUDA;
+    const int res = ((L.bits + 7) / 8) & 1;
+    float4 *spos = at<float4>(workspace, L.spos);
+    k_knn_ranges<<<ceil_div_u64(n, 256), 256, 0, s>>>(keys[res], vals[res], pos, n, at<uint2>(workspace, L.ranges),
+                                                     spos);
+    k_knn_query<<<ceil_div_u64(n, 128), 128, 0, s>>>(spos, at<uint2>(workspace, L.ranges), grid, n, knn);
+    return cudaGetLastError() == cudaSuccess ? GES_OK : GES_ERR_CUDA;
+}
