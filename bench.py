@@ -56,6 +56,7 @@ def parse_args():
     p.add_argument("--batch", type=int, default=None, help="fix the prefetch distance (skips the autotuner)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-train-step", action="store_true", help="skip the step with the Eq. 8 loss")
+    p.add_argument("--no-gsr", action="store_true", help="skip the KNN build and GSR point evaluation")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the oracle sample")
     p.add_argument("--splats", type=int, default=None,
                    help="override the workload's splat count (smaller cases for profiling; not a bench line)")
@@ -467,6 +468,48 @@ def main():
         del tplan
         torch.cuda.empty_cache()
 
+    # GSR point evaluation (Eq. 9-13): one sample per splat, KNN-16 lists built on the device
+    gsr = None
+    if not args.no_gsr:
+        n = sc.n
+        kws = torch.empty(api.ges_knn_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+        knn = torch.empty((n, 16), dtype=torch.int32, device="cuda")
+        gen = torch.Generator(device="cuda").manual_seed(3000 + rank)
+        js = torch.arange(n, dtype=torch.int32, device="cuda")
+        zs = torch.randn((n, 3), generator=gen, device="cuda")
+        gws = torch.empty(api.ges_gsr_workspace_bytes(n, n), dtype=torch.uint8, device="cuda")
+        losses = torch.empty(3, device="cuda")
+        gg = [torch.empty_like(t) for t in inputs[:3]]
+        cfg_c = cfg.to_c()
+
+        def timed(fn):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return max_over_ranks(statistics.mean(ts), world)
+
+        knn_ms = timed(lambda: api.ges_knn(n, inputs[0], kws, knn))
+        fwd_ms = timed(lambda: api.ges_gsr(n, inputs[0], inputs[1], inputs[2], cfg_c, knn, n, js, zs, 1.0, 1.0, gws,
+                                            losses))
+        fb_ms = timed(lambda: api.ges_gsr(n, inputs[0], inputs[1], inputs[2], cfg_c, knn, n, js, zs, 1.0, 1.0, gws,
+                                           losses, None, *gg))
+        gsr = {"value": world * n / (fb_ms / 1e3) / 1e6, "unit": "Msample/s", "samples": n,
+               "gsr_fwd_bwd_ms": fb_ms, "gsr_fwd_ms": fwd_ms, "knn_ms": knn_ms,
+               "losses": [round(float(x), 6) for x in losses.cpu().tolist()],
+               "sampling": "one sample per splat, z ~ N(0, I), neighbours = the splat's 16 nearest centres",
+               "gpu_launches": args.steps * ((6 + 5 * (((2 * n - 1).bit_length() + 7) // 8)) + 3 + 4)}
+        del kws, knn, gws, gg
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, npx, secs, cores = cpu_baseline(sc, cams, cfg, args.cpu_seconds)
@@ -490,6 +533,7 @@ def main():
             "per_view": per_view,
             "e2e": e2e,
             "train_step": train,
+            "gsr": gsr,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": plan.launches_per_step() * args.steps,
