@@ -1,0 +1,74 @@
+"""Pins of the level-set extraction oracle (oracle/levelset.py): the ray and its start point
+against the camera projection, the crossing of an isolated flat splat against its closed form,
+its normal, sigma_g(v) along a principal axis, and the cases without a point."""
+import numpy as np
+from scipy.spatial.transform import Rotation
+
+from oracle import levelset as OLS
+
+
+def _cam(w=64, h=48, f=50.0, R=np.eye(3), t=np.array([0.0, 0.0, 4.0])):
+    vm = np.concatenate([R, t[:, None]], 1)
+    return dict(width=w, height=h, fx=f, fy=f, cx=w / 2, cy=h / 2, viewmat=vm.reshape(-1))
+
+
+def _scene(centre, ls, q, o=1.0, beta=2.0):
+    # splat 0 at the centre, 16 far splats of zero opacity
+    pos = np.zeros((17, 4))
+    pos[0, :3], pos[0, 3] = centre, o
+    pos[1:, :3] = 100.0 + np.arange(16)[:, None]
+    lsb = np.zeros((17, 4))
+    lsb[:, :3], lsb[:, 3] = ls, beta
+    return pos, lsb, np.tile(q, (17, 1))
+
+
+def test_start_point_projects_to_the_pixel_at_the_rendered_depth():
+    R = Rotation.from_euler("xyz", [0.2, -0.3, 0.1]).as_matrix()
+    cam = _cam(R=R, t=np.array([0.1, -0.2, 3.5]))
+    pos, lsb, q = _scene([0.0, 0.0, 0.0], [-2.0, -2.0, -2.0], [1.0, 0, 0, 0])
+    out = OLS.extract(pos, lsb, q, cam, depth=1.8, alpha=0.6, px=20, py=31)
+    pc = R @ out["x0"] + np.array([0.1, -0.2, 3.5])
+    assert abs(pc[2] - 3.0) < 1e-12  # D / A
+    np.testing.assert_allclose([50 * pc[0] / pc[2] + 32, 50 * pc[1] / pc[2] + 24], [20.5, 31.5], atol=1e-10)
+
+
+def test_isolated_flat_splat_crossing_and_normal():
+    # a flat Gaussian splat facing the camera, its centre on the optical axis at depth 4: along
+    # the axis d(t) = o exp(-(t / s)^2 / 2), first reaching 0.3 at t = -s sqrt(2 ln(o / 0.3))
+    o, s = 0.9, 0.02
+    pos, lsb, q = _scene([0.0, 0.0, 0.0], [np.log(0.5), np.log(0.5), np.log(s)], [1.0, 0, 0, 0], o=o)
+    cam = _cam(w=64, h=64)
+    # pixel (31, 31)'s centre is 0.5 px off the axis: at depth 4 that is 0.04, far inside the 0.5 scales
+    out = OLS.extract(pos, lsb, q, cam, depth=4.0, alpha=1.0, px=32, py=32, n_steps=4001, phi_mode=0)
+    assert out["valid"] and not out["flag"]
+    _, v, _ = OLS.ray(cam, 32, 32)
+    x0 = out["x0"]
+    # along this slightly oblique ray the flat axis is z: d = o exp(-1/2 (Q_inplane + (z / s)^2))
+    qin = (x0[0] + out["t"] * v[0]) ** 2 / 0.25 + (x0[1] + out["t"] * v[1]) ** 2 / 0.25
+    z = x0[2] + out["t"] * v[2]
+    d = o * np.exp(-0.5 * (qin + (z / s) ** 2))
+    assert abs(d - 0.3) < 2e-4
+    assert z < 0  # the camera side: the camera sits at z = -4 in the world
+    # normal: -grad d points away from the splat, toward the camera side
+    A = np.diag([4.0, 4.0, 1 / s ** 2])
+    g = A @ out["point"]
+    np.testing.assert_allclose(out["normal"], g / np.linalg.norm(g), atol=1e-10)
+
+
+def test_sigma_along_a_principal_axis():
+    R = Rotation.from_euler("z", 0.7).as_matrix()
+    q = Rotation.from_matrix(R).as_quat()[[3, 0, 1, 2]]
+    pos, lsb, _ = _scene([0.0, 0.0, 0.0], [np.log(0.3), np.log(0.2), np.log(0.05)], q)
+    q = np.tile(q, (17, 1))
+    cam = _cam(w=64, h=64)
+    out = OLS.extract(pos, lsb, q, cam, depth=4.0, alpha=1.0, px=32, py=32, phi_mode=0)
+    _, v, _ = OLS.ray(cam, 32, 32)
+    loc = R.T @ v
+    np.testing.assert_allclose(out["sigma"], np.sqrt(((loc * [0.3, 0.2, 0.05]) ** 2).sum()), rtol=1e-12)
+
+
+def test_no_point_without_coverage_or_crossing():
+    pos, lsb, q = _scene([0.0, 0.0, 0.0], [-2.0, -2.0, -4.0], [1.0, 0, 0, 0], o=0.2)  # peak below the level
+    cam = _cam(w=64, h=64)
+    assert not OLS.extract(pos, lsb, q, cam, depth=4.0, alpha=1.0, px=32, py=32)["valid"]
+    assert not OLS.extract(pos, lsb, q, cam, depth=4.0, alpha=5e-5, px=32, py=32)["valid"]
