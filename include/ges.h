@@ -334,6 +334,31 @@ GES_API ges_status ges_knn(int32_t n, const float *pos_op, void *workspace, size
  * three NULL for the losses only. Workspace: ges_gsr_workspace_bytes(n, m) bytes,
  * 256-byte aligned, no initialisation needed. Gradient sums use float atomics, so
  * their last bits vary from run to run; the losses are summed in a fixed order. */
+/* ---------------------------------------------------------------- level-set points
+ * Isosurface points with normals from rendered depth (Sec. 3.3, "Mesh Extraction"; the
+ * paper's level is 0.3, Sec. 4.2), the input of a Poisson reconstruction. For each of the
+ * m sampled pixels (pixels [m, 2] int32: view, pixel index y * W + x):
+ *  - x0 = the point on the ray through the pixel centre at camera depth D / A, with D and
+ *    A the pixel's rendered depth and alpha (depth, alpha: ges_render_fwd's outputs, all
+ *    views concatenated); pixels with A < 1e-4, a non-finite x0, a view outside 0..n_views-1
+ *    or an index outside their view give no point. v = the ray's unit direction.
+ *  - the density of Eq. 9 along the ray is summed over the GES_KNN_K splats whose centres
+ *    are nearest to x0 (the same 16 for the whole ray);
+ *  - g = the one of them with the largest falloff at x0; the ray is sampled at n_steps
+ *    (2..1024) evenly spaced t in [-3 sigma, 3 sigma], sigma^2 = v^T Sigma_g v;
+ *  - the point is the first crossing from the camera side, d(t_k) < level <= d(t_k+1),
+ *    linearly interpolated; the normal is grad f / |grad f| there (the direction of
+ *    -grad d, summed relative to its largest term).
+ * points [m, 8] float32 (written): x, y, z, nx, ny, nz, t, valid (1 or 0; the other
+ * fields are 0 when there is no point). cfg: phi_mode and rho as in the rasterizer.
+ * Workspace: ges_levelset_workspace_bytes(n, m) bytes, 256-byte aligned, no
+ * initialisation needed. */
+GES_API size_t ges_levelset_workspace_bytes(int32_t n, int32_t m);
+GES_API ges_status ges_levelset(int32_t n, const float *pos_op, const float *lscale_beta, const float *quat,
+                                const ges_config *cfg, int32_t n_views, const ges_camera *cams, const float *depth,
+                                const float *alpha, int32_t m, const int32_t *pixels, int32_t n_steps, float level,
+                                void *workspace, size_t workspace_bytes, float *points, void *stream);
+
 GES_API size_t ges_gsr_workspace_bytes(int32_t n, int32_t m);
 GES_API ges_status ges_gsr(int32_t n, const float *pos_op, const float *lscale_beta, const float *quat,
                            const ges_config *cfg, const int32_t *knn, int32_t m, const int32_t *sample_splat,

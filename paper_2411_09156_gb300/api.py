@@ -260,6 +260,36 @@ def gsr(pos_op, lscale_beta, quat, knn_idx, sample_splat, sample_z, cfg: Optiona
     return dict(losses=losses, g_pos_op=g[0], g_lscale_beta=g[1], g_quat=g[2], sample_out=so)
 
 
+def ges_levelset_workspace_bytes(n: int, m: int) -> int:
+    nb = int(_lib.lib().ges_levelset_workspace_bytes(n, m))
+    if nb == 0:
+        raise ValueError("invalid sizes for ges_levelset")
+    return nb
+
+
+def ges_levelset(n, pos_op, lscale_beta, quat, cfg_c, n_views, cams_c, depth, alpha, m, pixels, n_steps, level,
+                 workspace, points, stream=None) -> None:
+    """Isosurface points and normals (Sec. 3.3) for m sampled pixels into points [m, 8]."""
+    check(_lib.lib().ges_levelset(n, _ptr(pos_op), _ptr(lscale_beta), _ptr(quat), ctypes.byref(cfg_c), n_views,
+                                  cams_c, _ptr(depth), _ptr(alpha), m, _ptr(pixels), int(n_steps), float(level),
+                                  _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(points),
+                                  _stream(stream)), "ges_levelset")
+
+
+def levelset(pos_op, lscale_beta, quat, cams, depth, alpha, pixels, n_steps: int = 32, level: float = 0.3,
+             cfg: Optional["GESConfig"] = None, stream=None) -> torch.Tensor:
+    """[m, 8] isosurface points (x, y, z, normal, t, valid) of the sampled pixels ([m, 2] int32:
+    view, y * W + x) of rendered views (depth, alpha: ges_render_fwd's outputs)."""
+    cfg = cfg or GESConfig()
+    n, m = pos_op.shape[0], pixels.shape[0]
+    cams_c = cameras_to_c(cams)
+    ws = torch.empty(ges_levelset_workspace_bytes(n, m), dtype=torch.uint8, device=pos_op.device)
+    out = torch.empty((m, 8), dtype=torch.float32, device=pos_op.device)
+    ges_levelset(n, pos_op, lscale_beta, quat, cfg.to_c(), len(cams), cams_c, depth, alpha, m, pixels, n_steps,
+                 level, ws, out, stream)
+    return out
+
+
 def ges_sync_status(proj, stream=None) -> int:
     """Synchronises the stream; returns (and clears) the device-recorded status code."""
     return int(_lib.lib().ges_sync_status(_ptr(proj), proj.numel(), _stream(stream)))

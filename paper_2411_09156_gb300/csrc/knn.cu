@@ -166,18 +166,12 @@ __device__ __forceinline__ float dist2(float4 a, float4 b) {
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
-__global__ void __launch_bounds__(128) k_knn_query(const float4 *spos, const uint2 *ranges, const KnnGrid *gp, int n,
-                                                   int32_t *knn) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const KnnGrid G = *gp;
-    const float4 p = spos[r];
-    const uint32_t self = __float_as_uint(p.w);
+// Ring search around point p for its kK nearest centres (lists in bd / bi, sorted).
+__device__ __forceinline__ void ring_search(float4 p, const KnnGrid &G, const uint2 *ranges, const float4 *spos,
+                                            float (&bd)[kK], uint32_t (&bi)[kK]) {
     const int c[3] = {cell_axis(p.x, G.lo[0], G.inv_h, G.dims[0]), cell_axis(p.y, G.lo[1], G.inv_h, G.dims[1]),
                       cell_axis(p.z, G.lo[2], G.inv_h, G.dims[2])};
     const float pc[3] = {p.x, p.y, p.z};
-    float bd[kK];
-    uint32_t bi[kK];
 #pragma unroll
     for (int k = 0; k < kK; ++k) { bd[k] = __int_as_float(0x7f800000); bi[k] = 0xffffffffu; }
     const int rmax = max(max(G.dims[0], G.dims[1]), G.dims[2]);
@@ -219,7 +213,8 @@ __global__ void __launch_bounds__(128) k_knn_query(const float4 *spos, const uin
                 }
             }
         }
-        // every point outside the searched block is at least `bound` away
+        // every point outside the searched block is at least `bound` away (a query outside
+        // the grid's box gets no early bound on that side and searches on)
         float bound = __int_as_float(0x7f800000);
         bool all = true;
 #pragma unroll
@@ -234,7 +229,36 @@ __global__ void __launch_bounds__(128) k_knn_query(const float4 *spos, const uin
         bound = fmaxf(bound, 0.f);
         if (bi[kK - 1] != 0xffffffffu && bd[kK - 1] <= bound * bound * (1.f - 1.f / 1048576.f)) break;
     }
-    int32_t *out = knn + (size_t)self * kK;
+}
+
+__global__ void __launch_bounds__(128) k_knn_query(const float4 *spos, const uint2 *ranges, const KnnGrid *gp, int n,
+                                                   int32_t *knn) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float4 p = spos[r];
+    float bd[kK];
+    uint32_t bi[kK];
+    ring_search(p, *gp, ranges, spos, bd, bi);
+    int32_t *out = knn + (size_t)__float_as_uint(p.w) * kK;
+#pragma unroll
+    for (int k = 0; k < kK; ++k) out[k] = (int32_t)bi[k];
+}
+
+// Queries at arbitrary points (w = 0: no query, the list is all -1).
+__global__ void __launch_bounds__(128) k_knn_points(const float4 *spos, const uint2 *ranges, const KnnGrid *gp,
+                                                    const float4 *pts, int m, int32_t *knn) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    const float4 p = pts[r];
+    float bd[kK];
+    uint32_t bi[kK];
+    if (p.w != 0.f) {
+        ring_search(p, *gp, ranges, spos, bd, bi);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kK; ++k) bi[k] = 0xffffffffu;
+    }
+    int32_t *out = knn + (size_t)r * kK;
 #pragma unroll
     for (int k = 0; k < kK; ++k) out[k] = (int32_t)bi[k];
 }
@@ -254,6 +278,44 @@ extern "C" size_t ges_knn_workspace_bytes(int32_t n) {
     return knn_layout(n).bytes;
 }
 
+namespace ges {
+
+// Grid, cell sort and cell-ordered centres of n splats in `workspace` (knn_workspace(n) bytes).
+static cudaError_t knn_build(int32_t n, const float4 *pos, void *workspace, const KnnLayout &L, cudaStream_t s) {
+    uint32_t *bb = at<uint32_t>(workspace, L.bbox);
+    KnnGrid *grid = at<KnnGrid>(workspace, L.grid);
+    cudaError_t e = cudaMemsetAsync(bb, 0xff, 12, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bb + 3, 0, 12, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(at<void>(workspace, L.ranges), 0, 8ull * L.cap_cells, s);
+    if (e != cudaSuccess) return e;
+    k_knn_bbox<<<min(ceil_div_u64(n, 256), 1024u), 256, 0, s>>>(pos, n, bb);
+    k_knn_grid<<<1, 1, 0, s>>>(bb, L.cap_cells, grid);
+    uint32_t *keys[2] = {at<uint32_t>(workspace, L.keys0), at<uint32_t>(workspace, L.keys1)};
+    uint32_t *vals[2] = {at<uint32_t>(workspace, L.vals0), at<uint32_t>(workspace, L.vals1)};
+    k_knn_keys<<<ceil_div_u64(n, 256), 256, 0, s>>>(pos, n, grid, keys[0]);
+    e = radix_sort(keys, vals, true, nullptr, (uint32_t)n, L.bits, at<uint32_t>(workspace, L.hist),
+                   at<uint32_t>(workspace, L.partials), s);
+    if (e != cudaSuccess) return e;
+    const int res = ((L.bits + 7) / 8) & 1;
+    k_knn_ranges<<<ceil_div_u64(n, 256), 256, 0, s>>>(keys[res], vals[res], pos, n, at<uint2>(workspace, L.ranges),
+                                                     at<float4>(workspace, L.spos));
+    return cudaGetLastError();
+}
+
+size_t knn_workspace(int32_t n) { return knn_layout(n).bytes; }
+
+cudaError_t knn_points_run(int32_t n, const float4 *pos, int32_t m, const float4 *pts, void *workspace,
+                           int32_t *knn, cudaStream_t s) {
+    const KnnLayout L = knn_layout(n);
+    cudaError_t e = knn_build(n, pos, workspace, L, s);
+    if (e != cudaSuccess || m <= 0) return e;
+    k_knn_points<<<ceil_div_u64(m, 128), 128, 0, s>>>(at<float4>(workspace, L.spos), at<uint2>(workspace, L.ranges),
+                                                     at<KnnGrid>(workspace, L.grid), pts, m, knn);
+    return cudaGetLastError();
+}
+
+}  // namespace ges
+
 extern "C" ges_status ges_knn(int32_t n, const float *pos_op, void *workspace, size_t workspace_bytes, int32_t *knn,
                               void *stream) {
     if (n < GES_KNN_K || (uint64_t)n > (1ull << 26) || !pos_op || !workspace || !knn) return GES_ERR_INVALID_ARG;
@@ -263,24 +325,8 @@ extern "C" ges_status ges_knn(int32_t n, const float *pos_op, void *workspace, s
     if (workspace_bytes < L.bytes) return GES_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const float4 *pos = reinterpret_cast<const float4 *>(pos_op);
-    uint32_t *bb = at<uint32_t>(workspace, L.bbox);
-    KnnGrid *grid = at<KnnGrid>(workspace, L.grid);
-    cudaError_t e = cudaMemsetAsync(bb, 0xff, 12, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(bb + 3, 0, 12, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(at<void>(workspace, L.ranges), 0, 8ull * L.cap_cells, s);
-    if (e != cudaSuccess) return GES_ERR_CUDA;
-    k_knn_bbox<<<min(ceil_div_u64(n, 256), 1024u), 256, 0, s>>>(pos, n, bb);
-    k_knn_grid<<<1, 1, 0, s>>>(bb, L.cap_cells, grid);
-    uint32_t *keys[2] = {at<uint32_t>(workspace, L.keys0), at<uint32_t>(workspace, L.keys1)};
-    uint32_t *vals[2] = {at<uint32_t>(workspace, L.vals0), at<uint32_t>(workspace, L.vals1)};
-    k_knn_keys<<<ceil_div_u64(n, 256), 256, 0, s>>>(pos, n, grid, keys[0]);
-    e = radix_sort(keys, vals, true, nullptr, (uint32_t)n, L.bits, at<uint32_t>(workspace, L.hist),
-                   at<uint32_t>(workspace, L.partials), s);
-    if (e != cudaSuccess) return GES_ERR_CUDA;
-    const int res = ((L.bits + 7) / 8) & 1;
-    float4 *spos = at<float4>(workspace, L.spos);
-    k_knn_ranges<<<ceil_div_u64(n, 256), 256, 0, s>>>(keys[res], vals[res], pos, n, at<uint2>(workspace, L.ranges),
-                                                     spos);
-    k_knn_query<<<ceil_div_u64(n, 128), 128, 0, s>>>(spos, at<uint2>(workspace, L.ranges), grid, n, knn);
+    if (knn_build(n, pos, workspace, L, s) != cudaSuccess) return GES_ERR_CUDA;
+    k_knn_query<<<ceil_div_u64(n, 128), 128, 0, s>>>(at<float4>(workspace, L.spos), at<uint2>(workspace, L.ranges),
+                                                    at<KnnGrid>(workspace, L.grid), n, knn);
     return cudaGetLastError() == cudaSuccess ? GES_OK : GES_ERR_CUDA;
 }
