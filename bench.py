@@ -56,7 +56,7 @@ def parse_args():
     p.add_argument("--batch", type=int, default=None, help="fix the prefetch distance (skips the autotuner)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-train-step", action="store_true", help="skip the step with the Eq. 8 loss")
-    p.add_argument("--no-gsr", action="store_true", help="skip the KNN build and GSR point evaluation")
+    p.add_argument("--no-gsr", action="store_true", help="skip the KNN build, the GSR point evaluation and the level-set extraction")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the oracle sample")
     p.add_argument("--splats", type=int, default=None,
                    help="override the workload's splat count (smaller cases for profiling; not a bench line)")
@@ -171,6 +171,15 @@ def kernel_source_sha256() -> str:
     for f in ("render.cu", "ges_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2411_09156_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
+
+
+def levelset_launches(n: int) -> int:
+    """Kernels one ges_levelset call launches: start points, splat records, the grid build
+    (bounding box, grid, cell keys, ranges, 5 per 8-bit radix pass), the query keys and their
+    radix sort, the point queries and the march."""
+    p_n = ((2 * n - 1).bit_length() + 7) // 8
+    p_q = ((2 * n).bit_length() + 7) // 8
+    return 8 + 5 * p_n + 5 * p_q
 
 
 def profile_traffic(kernel: str):
@@ -510,6 +519,29 @@ def main():
         del kws, knn, gws, gg
         torch.cuda.empty_cache()
 
+    # level-set points (Sec. 3.3, level 0.3) from the rendered depth / alpha of every pixel of the
+    # batch's views: start points, KNN point queries, the density march and the normals
+    levelset = None
+    if not args.no_gsr:
+        n = sc.n
+        o = plan.rast.out
+        pix = torch.cat([torch.stack([torch.full((c.width * c.height,), v, dtype=torch.int32, device="cuda"),
+                                      torch.arange(c.width * c.height, dtype=torch.int32, device="cuda")], 1)
+                         for v, c in enumerate(cams)]).contiguous()
+        lws = torch.empty(api.ges_levelset_workspace_bytes(n, P), dtype=torch.uint8, device="cuda")
+        pts = torch.empty((P, 8), dtype=torch.float32, device="cuda")
+        cams_c = api.cameras_to_c(cams)
+        cfg_c = cfg.to_c()
+        ls_ms = timed(lambda: api.ges_levelset(n, inputs[0], inputs[1], inputs[2], cfg_c, len(cams), cams_c,
+                                               o["depth"], o["alpha"], P, pix, 32, 0.3, lws, pts))
+        n_pts = int(pts[:, 7].sum().item())
+        levelset = {"value": world * P / (ls_ms / 1e3) / 1e6, "unit": "Mpixel/s", "pixels": P, "points": n_pts,
+                    "levelset_ms": ls_ms, "n_steps": 32, "level": 0.3,
+                    "sampling": "every pixel of the batch's views, depth / alpha from the rendered step",
+                    "gpu_launches": args.steps * levelset_launches(n)}
+        del lws, pts, pix
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, npx, secs, cores = cpu_baseline(sc, cams, cfg, args.cpu_seconds)
@@ -534,6 +566,7 @@ def main():
             "e2e": e2e,
             "train_step": train,
             "gsr": gsr,
+            "levelset": levelset,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": plan.launches_per_step() * args.steps,

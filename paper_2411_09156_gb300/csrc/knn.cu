@@ -7,8 +7,10 @@
 // Each query then walks Chebyshev rings of cells around its own cell, keeping its 16
 // best (distance, index) pairs sorted in registers, and stops once the 16th best
 // distance is within the distance from the query to the outside of the searched
-// block (no unsearched point can be closer). Queries run in cell order, so a warp
-// searches one neighbourhood. Distances are squared float32 with a fixed operation
+// block (no unsearched point can be closer). Once it holds 16, rows and cells whose box
+// lies farther than the 16th are skipped without reading their ranges (what keeps queries
+// away from the centres, such as points in front of a surface, from reading every cell of
+// their block). Queries run in cell order, so a warp searches one neighbourhood. Distances are squared float32 with a fixed operation
 // order; ties go to the lower index. A query examines at most 65,536 candidates (a
 // bound that well-spread centres never reach; tens of thousands of coincident
 // centres would), so no input makes the search quadratic.
@@ -28,6 +30,7 @@ struct KnnGrid {
     float lo[3];
     float h, inv_h;
     int dims[3];
+    float slack;  // bound on how far float32 rounding can put a point outside its cell's box
 };
 
 struct KnnLayout {
@@ -131,6 +134,9 @@ __global__ void k_knn_grid(const uint32_t *bb, uint32_t cap, KnnGrid *g) {
     }
     g->h = h;
     g->inv_h = 1.f / h;
+    float amax = 0.f;
+    for (int k = 0; k < 3; ++k) amax = fmaxf(amax, fabsf(g->lo[k]) + (float)d[k] * h);
+    g->slack = 4e-6f * amax;
 }
 
 __device__ __forceinline__ int cell_axis(float p, float lo, float inv_h, int dim) {
@@ -175,12 +181,21 @@ __device__ __forceinline__ void ring_search(float4 p, const KnnGrid &G, const ui
 #pragma unroll
     for (int k = 0; k < kK; ++k) { bd[k] = __int_as_float(0x7f800000); bi[k] = 0xffffffffu; }
     const int rmax = max(max(G.dims[0], G.dims[1]), G.dims[2]);
+    // distance along axis k from p to cell index ci's slab, less the rounding slack; once 16
+    // are held, a row or cell whose box is farther than the 16th is skipped unread
+    auto gap = [&](int k, int ci) {
+        const float a = G.lo[k] + (float)ci * G.h - G.slack - pc[k];
+        const float b = pc[k] - (G.lo[k] + (float)(ci + 1) * G.h + G.slack);
+        return fmaxf(fmaxf(a, b), 0.f);
+    };
     uint32_t examined = 0;
     for (int ring = 0; ring <= rmax && examined < kQueryBudget; ++ring) {
         const int z0 = max(c[2] - ring, 0), z1 = min(c[2] + ring, G.dims[2] - 1);
         const int y0 = max(c[1] - ring, 0), y1 = min(c[1] + ring, G.dims[1] - 1);
         const int x0 = max(c[0] - ring, 0), x1 = min(c[0] + ring, G.dims[0] - 1);
-        auto visit = [&](int cx, int cy, int cz) {
+        auto visit = [&](int cx, int cy, int cz, float gyz) {
+            const float gx = gap(0, cx);
+            if (fmaf(gx, gx, gyz) > bd[kK - 1]) return;
             const uint2 rg = __ldg(ranges + (cx + G.dims[0] * (cy + G.dims[1] * cz)));
             const uint32_t end = min(rg.y, rg.x + (kQueryBudget - min(examined, kQueryBudget)));
             examined += rg.y - rg.x;
@@ -204,12 +219,17 @@ __device__ __forceinline__ void ring_search(float4 p, const KnnGrid &G, const ui
         };
         // the cells at Chebyshev distance `ring` from the query's cell
         for (int cz = z0; cz <= z1; ++cz) {
+            const float gz = gap(2, cz);
+            if (gz * gz > bd[kK - 1]) continue;
             for (int cy = y0; cy <= y1; ++cy) {
+                const float gy = gap(1, cy);
+                const float gyz = fmaf(gy, gy, gz * gz);
+                if (gyz > bd[kK - 1]) continue;
                 if (abs(cz - c[2]) < ring && abs(cy - c[1]) < ring) {  // only the two x faces are new
-                    if (c[0] - ring >= 0) visit(c[0] - ring, cy, cz);
-                    if (c[0] + ring < G.dims[0]) visit(c[0] + ring, cy, cz);
+                    if (c[0] - ring >= 0) visit(c[0] - ring, cy, cz, gyz);
+                    if (c[0] + ring < G.dims[0]) visit(c[0] + ring, cy, cz, gyz);
                 } else {
-                    for (int cx = x0; cx <= x1; ++cx) visit(cx, cy, cz);
+                    for (int cx = x0; cx <= x1; ++cx) visit(cx, cy, cz, gyz);
                 }
             }
         }
@@ -226,7 +246,7 @@ __device__ __forceinline__ void ring_search(float4 p, const KnnGrid &G, const ui
             }
         }
         if (all) break;
-        bound = fmaxf(bound, 0.f);
+        bound = fmaxf(bound - G.slack, 0.f);
         if (bi[kK - 1] != 0xffffffffu && bd[kK - 1] <= bound * bound * (1.f - 1.f / 1048576.f)) break;
     }
 }
@@ -244,11 +264,26 @@ __global__ void __launch_bounds__(128) k_knn_query(const float4 *spos, const uin
     for (int k = 0; k < kK; ++k) out[k] = (int32_t)bi[k];
 }
 
-// Queries at arbitrary points (w = 0: no query, the list is all -1).
-__global__ void __launch_bounds__(128) k_knn_points(const float4 *spos, const uint2 *ranges, const KnnGrid *gp,
-                                                    const float4 *pts, int m, int32_t *knn) {
+// Cell keys of query points (w = 0: no query, sorted after every cell).
+__global__ void __launch_bounds__(256) k_knn_point_keys(const float4 *pts, int m, const KnnGrid *g, uint32_t none,
+                                                        uint32_t *keys) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= m) return;
+    const float4 p = pts[r];
+    const KnnGrid G = *g;
+    keys[r] = p.w == 0.f ? none
+                         : (uint32_t)(cell_axis(p.x, G.lo[0], G.inv_h, G.dims[0]) +
+                                      G.dims[0] * (cell_axis(p.y, G.lo[1], G.inv_h, G.dims[1]) +
+                                                   G.dims[1] * cell_axis(p.z, G.lo[2], G.inv_h, G.dims[2])));
+}
+
+// Queries at arbitrary points, taken in cell order (order[r]: the r-th query by cell), so a
+// warp searches one neighbourhood; w = 0: no query, the list is all -1.
+__global__ void __launch_bounds__(128) k_knn_points(const float4 *spos, const uint2 *ranges, const KnnGrid *gp,
+                                                    const float4 *pts, const uint32_t *order, int m, int32_t *knn) {
+    const int r0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r0 >= m) return;
+    const uint32_t r = __ldg(order + r0);
     const float4 p = pts[r];
     float bd[kK];
     uint32_t bi[kK];
@@ -258,9 +293,33 @@ __global__ void __launch_bounds__(128) k_knn_points(const float4 *spos, const ui
 #pragma unroll
         for (int k = 0; k < kK; ++k) bi[k] = 0xffffffffu;
     }
-    int32_t *out = knn + (size_t)r * kK;
+    int4 *out = reinterpret_cast<int4 *>(knn + (size_t)r * kK);
 #pragma unroll
-    for (int k = 0; k < kK; ++k) out[k] = (int32_t)bi[k];
+    for (int k = 0; k < kK; k += 4)
+        out[k / 4] = make_int4((int32_t)bi[k], (int32_t)bi[k + 1], (int32_t)bi[k + 2], (int32_t)bi[k + 3]);
+}
+
+// Cell sort of m query points, after the grid's own workspace.
+struct KnnQueryLayout {
+    uint64_t keys0, keys1, vals0, vals1, hist, partials, bytes;
+    uint32_t nblocks;
+    int bits;
+};
+
+KnnQueryLayout knn_query_layout(uint32_t cap_cells, int32_t m) {
+    KnnQueryLayout Q;
+    Q.bits = 1;
+    while ((1ull << Q.bits) <= cap_cells) ++Q.bits;  // every cell index and the "no query" key fit
+    Q.nblocks = ceil_div_u64(m > 0 ? (uint64_t)m : 1, kSortTile);
+    uint64_t off = 0;
+    Q.keys0 = off; off = al256(off + 4ull * m);
+    Q.keys1 = off; off = al256(off + 4ull * m);
+    Q.vals0 = off; off = al256(off + 4ull * m);
+    Q.vals1 = off; off = al256(off + 4ull * m);
+    Q.hist = off; off = al256(off + 4ull * 256 * Q.nblocks);
+    Q.partials = off; off = al256(off + 4ull * (ceil_div_u64(256ull * Q.nblocks, kScanTile) + 1));
+    Q.bytes = off;
+    return Q;
 }
 
 template <class T>
@@ -280,7 +339,7 @@ extern "C" size_t ges_knn_workspace_bytes(int32_t n) {
 
 namespace ges {
 
-// Grid, cell sort and cell-ordered centres of n splats in `workspace` (knn_workspace(n) bytes).
+// Grid, cell sort and cell-ordered centres of n splats in `workspace` (knn_layout(n).bytes).
 static cudaError_t knn_build(int32_t n, const float4 *pos, void *workspace, const KnnLayout &L, cudaStream_t s) {
     uint32_t *bb = at<uint32_t>(workspace, L.bbox);
     KnnGrid *grid = at<KnnGrid>(workspace, L.grid);
@@ -302,15 +361,31 @@ static cudaError_t knn_build(int32_t n, const float4 *pos, void *workspace, cons
     return cudaGetLastError();
 }
 
-size_t knn_workspace(int32_t n) { return knn_layout(n).bytes; }
+// Workspace of knn_points_run: the grid of n centres, then the cell sort of m queries.
+size_t knn_points_workspace(int32_t n, int32_t m) {
+    const KnnLayout L = knn_layout(n);
+    return L.bytes + knn_query_layout(L.cap_cells, m).bytes;
+}
 
+// The 16 nearest centres of m points (pts[i].w = 0: none, list -1) into knn [m][16]
+// (16-byte aligned); workspace: knn_points_workspace(n, m) bytes, 256-byte aligned.
 cudaError_t knn_points_run(int32_t n, const float4 *pos, int32_t m, const float4 *pts, void *workspace,
                            int32_t *knn, cudaStream_t s) {
     const KnnLayout L = knn_layout(n);
     cudaError_t e = knn_build(n, pos, workspace, L, s);
     if (e != cudaSuccess || m <= 0) return e;
+    const KnnQueryLayout Q = knn_query_layout(L.cap_cells, m);
+    void *qws = static_cast<char *>(workspace) + L.bytes;
+    uint32_t *keys[2] = {at<uint32_t>(qws, Q.keys0), at<uint32_t>(qws, Q.keys1)};
+    uint32_t *vals[2] = {at<uint32_t>(qws, Q.vals0), at<uint32_t>(qws, Q.vals1)};
+    k_knn_point_keys<<<ceil_div_u64(m, 256), 256, 0, s>>>(pts, m, at<KnnGrid>(workspace, L.grid),
+                                                          (uint32_t)((1ull << Q.bits) - 1), keys[0]);
+    e = radix_sort(keys, vals, true, nullptr, (uint32_t)m, Q.bits, at<uint32_t>(qws, Q.hist),
+                   at<uint32_t>(qws, Q.partials), s);
+    if (e != cudaSuccess) return e;
+    const int res = ((Q.bits + 7) / 8) & 1;
     k_knn_points<<<ceil_div_u64(m, 128), 128, 0, s>>>(at<float4>(workspace, L.spos), at<uint2>(workspace, L.ranges),
-                                                     at<KnnGrid>(workspace, L.grid), pts, m, knn);
+                                                     at<KnnGrid>(workspace, L.grid), pts, vals[res], m, knn);
     return cudaGetLastError();
 }
 

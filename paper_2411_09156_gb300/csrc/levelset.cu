@@ -5,7 +5,7 @@
 // by linear interpolation, and the normal grad f / |grad f| there.
 //
 // k_ls_start places x0 (depth D / A along the pixel ray); the KNN point queries of
-// knn.cu find the 16 nearest centres; k_ls_march, one thread per pixel, turns each
+// knn.cu (taken in grid-cell order) find the 16 nearest centres; k_ls_march, one thread per pixel, turns each
 // neighbour into the ray form of its axis coordinates, loc_k(t) = loc_k(x0) + t loc_k(v)
 // (shared memory, 8 floats per neighbour), so a step costs three fused multiply-adds
 // per axis and two exponentials per neighbour; the march stops at the first crossing.
@@ -16,7 +16,7 @@
 
 namespace ges {
 
-size_t knn_workspace(int32_t n);
+size_t knn_points_workspace(int32_t n, int32_t m);
 cudaError_t knn_points_run(int32_t n, const float4 *pos, int32_t m, const float4 *pts, void *workspace,
                            int32_t *knn, cudaStream_t s);
 
@@ -206,7 +206,7 @@ inline uint64_t al256l(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 LsLayout ls_layout(int32_t n, int32_t m) {
     LsLayout L;
     uint64_t off = 0;
-    L.knn_ws = off; off = al256l(off + knn_workspace(n));
+    L.knn_ws = off; off = al256l(off + knn_points_workspace(n, m));
     L.rec = off; off = al256l(off + 16ull * kRec * n);
     L.pts = off; off = al256l(off + 16ull * m);
     L.lists = off; off = al256l(off + 4ull * kK * m);
