@@ -6,14 +6,15 @@
 // sort of the binning), dense cell ranges and a cell-ordered copy of the centres.
 // Each query then walks Chebyshev rings of cells around its own cell, keeping its 16
 // best (distance, index) pairs sorted in registers, and stops once the 16th best
-// distance is within the distance from the query to the outside of the searched
-// block (no unsearched point can be closer). Once it holds 16, rows and cells whose box
-// lies farther than the 16th are skipped without reading their ranges (what keeps queries
-// away from the centres, such as points in front of a surface, from reading every cell of
-// their block). Queries run in cell order, so a warp searches one neighbourhood. Distances are squared float32 with a fixed operation
-// order; ties go to the lower index. A query examines at most 65,536 candidates (a
-// bound that well-spread centres never reach; tens of thousands of coincident
-// centres would), so no input makes the search quadratic.
+// distance is within the distance from the query to the part of the grid's box outside
+// the searched block (no unsearched point can be closer). Once it holds 16, rows and
+// cells whose box lies farther than the 16th are skipped without reading their ranges,
+// which keeps queries away from the centres (points in front of a surface) from reading
+// every cell of their block. Queries run in cell order, so a warp searches one
+// neighbourhood. Distances are squared float32 with a fixed operation order; ties go to
+// the lower index. A query examines at most 65,536 candidates (a bound that well-spread
+// centres never reach; tens of thousands of coincident centres would), so no input makes
+// the search quadratic.
 #include "ges_internal.cuh"
 
 namespace ges {
@@ -188,6 +189,12 @@ __device__ __forceinline__ void ring_search(float4 p, const KnnGrid &G, const ui
         const float b = pc[k] - (G.lo[k] + (float)(ci + 1) * G.h + G.slack);
         return fmaxf(fmaxf(a, b), 0.f);
     };
+    float outg[3], og2 = 0.f;  // distance from p to the grid's box along each axis, less the slack
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        outg[k] = fmaxf(fmaxf(G.lo[k] - G.slack - pc[k], pc[k] - (G.lo[k] + (float)G.dims[k] * G.h + G.slack)), 0.f);
+        og2 = fmaf(outg[k], outg[k], og2);
+    }
     uint32_t examined = 0;
     for (int ring = 0; ring <= rmax && examined < kQueryBudget; ++ring) {
         const int z0 = max(c[2] - ring, 0), z1 = min(c[2] + ring, G.dims[2] - 1);
@@ -233,21 +240,27 @@ __device__ __forceinline__ void ring_search(float4 p, const KnnGrid &G, const ui
                 }
             }
         }
-        // every point outside the searched block is at least `bound` away (a query outside
-        // the grid's box gets no early bound on that side and searches on)
-        float bound = __int_as_float(0x7f800000);
+        // every unsearched point lies in the grid's box beyond one of the searched block's open
+        // faces; b2 is the least squared distance from p to those regions (a query outside the
+        // box adds its distance to the box on the other axes)
+        float b2 = __int_as_float(0x7f800000);
         bool all = true;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            if (c[k] - ring > 0) { bound = fminf(bound, pc[k] - (G.lo[k] + (float)(c[k] - ring) * G.h)); all = false; }
+            const float others = og2 - outg[k] * outg[k];
+            if (c[k] - ring > 0) {
+                const float g = fmaxf(pc[k] - (G.lo[k] + (float)(c[k] - ring) * G.h) - G.slack, 0.f);
+                b2 = fminf(b2, fmaf(g, g, others));
+                all = false;
+            }
             if (c[k] + ring < G.dims[k] - 1) {
-                bound = fminf(bound, (G.lo[k] + (float)(c[k] + ring + 1) * G.h) - pc[k]);
+                const float g = fmaxf((G.lo[k] + (float)(c[k] + ring + 1) * G.h) - pc[k] - G.slack, 0.f);
+                b2 = fminf(b2, fmaf(g, g, others));
                 all = false;
             }
         }
         if (all) break;
-        bound = fmaxf(bound - G.slack, 0.f);
-        if (bi[kK - 1] != 0xffffffffu && bd[kK - 1] <= bound * bound * (1.f - 1.f / 1048576.f)) break;
+        if (bi[kK - 1] != 0xffffffffu && bd[kK - 1] <= b2 * (1.f - 1.f / 1048576.f)) break;
     }
 }
 
