@@ -56,6 +56,7 @@ def parse_args():
     p.add_argument("--batch", type=int, default=None, help="fix the prefetch distance (skips the autotuner)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-train-step", action="store_true", help="skip the step with the Eq. 8 loss")
+    p.add_argument("--no-color16", action="store_true", help="skip the step with binary16 colour storage")
     p.add_argument("--no-gsr", action="store_true", help="skip the KNN build, the GSR point evaluation and the level-set extraction")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the oracle sample")
     p.add_argument("--splats", type=int, default=None,
@@ -434,6 +435,36 @@ def main():
         e2e = {"value": world * P / (em / 1e3) / 1e6, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": em}
 
+    # precision variant: the colour input (SH coefficients) stored as IEEE binary16 and widened
+    # to float32 on load; the same batched step otherwise
+    color16 = None
+    if not args.no_color16 and sc.sh_degree >= 0:
+        c16 = inputs[3].half().contiguous()
+        plan16 = BatchPlan(sc.n, cams, dataclasses.replace(cfg, color_storage=1),
+                           [inputs[0], inputs[1], inputs[2], c16], ups, capacity=plan.capacity)
+        for _ in range(args.warmup):
+            plan16.step()
+        torch.cuda.synchronize()
+        plan16.check()
+        evs16 = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            plan16.step(evs16[k])
+        torch.cuda.synchronize()
+        if plan16.rast.sync_status() != 0:
+            raise RuntimeError("device status after the binary16-colour steps")
+        t16 = max_over_ranks(statistics.mean(evs16[k][0].elapsed_time(evs16[k][4]) for k in range(args.steps)),
+                             world)
+        st16 = [statistics.mean(evs16[k][i].elapsed_time(evs16[k][i + 1]) for k in range(args.steps))
+                for i in range(4)]
+        kc = (sc.sh_degree + 1) ** 2
+        color16 = {"value": world * P / (t16 / 1e3) / 1e6, "unit": "Mpixel/s", "ms_per_step": t16,
+                   "stages_ms": dict(zip(names, st16)), "color_storage": "binary16",
+                   "color_bytes_per_splat": {"float32": 12 * kc, "binary16": 6 * kc},
+                   "gpu_launches": plan16.launches_per_step() * args.steps}
+        del plan16, c16
+        torch.cuda.empty_cache()
+
     # training step: the same views with the Eq. 8 loss against target images between the render
     # passes (colour gradient from the loss instead of random upstream gradients)
     train = None
@@ -565,6 +596,7 @@ def main():
             "per_view": per_view,
             "e2e": e2e,
             "train_step": train,
+            "color_binary16": color16,
             "gsr": gsr,
             "levelset": levelset,
             "cpu_baseline": cpu,

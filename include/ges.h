@@ -73,7 +73,7 @@ extern "C" {
 #define GES_API
 #endif
 
-#define GES_ABI_VERSION 1
+#define GES_ABI_VERSION 2
 #define GES_MAX_VIEWS 32
 
 typedef enum ges_status {
@@ -110,6 +110,9 @@ typedef struct ges_config {
     float bg[3];            /* background colour */
     int32_t persistent;     /* 0: one CTA per tile; 1: persistent warps taking (tile, 8x4 block) items of a
                                longest-first tile queue */
+    int32_t color_storage;  /* element type of the colour input (`color` of ges_preprocess, `color_in` of the
+                               backward calls): 0 float32, 1 IEEE binary16, 2 bfloat16. The values are widened
+                               to float32 on load and everything after is float32; gradients stay float32 */
 } ges_config;
 
 /* Number of bytes `proj` must hold for n splats and n_views views:
@@ -128,12 +131,13 @@ GES_API size_t ges_bins_bytes(int32_t n, int32_t n_views, const ges_camera *cams
  *   pos_op      [n, 4]  x, y, z, opacity in (0, 1] (already activated)
  *   lscale_beta [n, 4]  log-scales l1, l2, l3 and beta > 0
  *   quat        [n, 4]  rotation (w, x, y, z), any non-zero norm
- *   color       [n, 3] RGB (sh_degree -1) or [n, (d+1)^2, 3] SH coefficients
+ *   color       [n, 3] RGB (sh_degree -1) or [n, (d+1)^2, 3] SH coefficients, float32 or the
+ *               16-bit type cfg->color_storage names; 16-byte aligned
  * cams: host array of n_views cameras (1 <= n_views <= GES_MAX_VIEWS).
  * Writes `proj` (ges_proj_bytes(n, n_views) bytes, 16-byte aligned), and the
  * total instance count read by ges_instance_count. Clears the error word. */
 GES_API ges_status ges_preprocess(int32_t n, const float *pos_op, const float *lscale_beta, const float *quat,
-                          const float *color, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                          const void *color, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
                           void *proj, size_t proj_bytes, void *stream);
 
 /* Synchronises `stream` and returns in *count the number of tile instances that
@@ -180,10 +184,11 @@ GES_API ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *
  * color, depth, normal, t_final and last, and the upstream gradients (same
  * layouts as the outputs; any of g_color, g_depth, g_alpha, g_normal may be NULL
  * for zero). Outputs g_pos_op, g_lscale_beta, g_quat, g_color_in have the input
- * layouts and are OVERWRITTEN (summed over views). g2d may be NULL, else it
+ * layouts (g_color_in in float32 whatever cfg->color_storage) and are OVERWRITTEN
+ * (summed over views). g2d may be NULL, else it
  * receives the per-entry screen-space gradients [n_views * n, 16]. */
 GES_API ges_status ges_render_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
-                          const float *pos_op, const float *lscale_beta, const float *quat, const float *color_in,
+                          const float *pos_op, const float *lscale_beta, const float *quat, const void *color_in,
                           void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes,
                           const float *color, const float *depth, const float *normal, const float *t_final,
                           const uint32_t *last, const float *g_color, const float *g_depth,
@@ -206,7 +211,7 @@ GES_API ges_status ges_render_bwd_screen(int32_t n, int32_t n_views, const ges_c
 
 GES_API ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
                                       const float *pos_op, const float *lscale_beta, const float *quat,
-                                      const float *color_in, const void *proj, size_t proj_bytes, const float *g2d,
+                                      const void *color_in, const void *proj, size_t proj_bytes, const float *g2d,
                                       float *g_pos_op, float *g_lscale_beta, float *g_quat, float *g_color_in,
                                       void *stream);
 
@@ -236,7 +241,7 @@ GES_API ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_came
 #define GES_NOALLOC_MAX_ENTRIES 524288
 GES_API ges_status ges_render_bwd_noalloc(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
                                           const float *pos_op, const float *lscale_beta, const float *quat,
-                                          const float *color_in, void *proj, size_t proj_bytes, const void *bins,
+                                          const void *color_in, void *proj, size_t proj_bytes, const void *bins,
                                           size_t bins_bytes, const float *color, const float *depth,
                                           const float *normal, const float *t_final, const uint32_t *last,
                                           const float *g_color, const float *g_depth, const float *g_alpha,

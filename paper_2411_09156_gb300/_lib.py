@@ -35,7 +35,7 @@ class Config(ctypes.Structure):
                 ("sh_degree", ctypes.c_int32), ("phi_mode", ctypes.c_int32), ("rho", ctypes.c_float),
                 ("lowpass", ctypes.c_float), ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("t_min", ctypes.c_float), ("jac_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3),
-                ("persistent", ctypes.c_int32)]
+                ("persistent", ctypes.c_int32), ("color_storage", ctypes.c_int32)]
 
 
 class Layout(ctypes.Structure):

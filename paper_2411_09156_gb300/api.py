@@ -36,10 +36,11 @@ class GESConfig:
     jac_clamp: float = 1.3
     bg: tuple = (0.0, 0.0, 0.0)
     persistent: int = 0
+    color_storage: int = 0  # colour input: 0 float32, 1 float16, 2 bfloat16
 
     def to_c(self) -> _lib.Config:
         c = _lib.Config()
-        for f in ("tile_w", "tile_h", "batch", "sh_degree", "phi_mode", "persistent"):
+        for f in ("tile_w", "tile_h", "batch", "sh_degree", "phi_mode", "persistent", "color_storage"):
             setattr(c, f, int(getattr(self, f)))
         for f in ("rho", "lowpass", "alpha_min", "alpha_max", "t_min", "jac_clamp"):
             setattr(c, f, float(getattr(self, f)))
@@ -49,6 +50,10 @@ class GESConfig:
 
     def replace(self, **kw) -> "GESConfig":
         return dataclasses.replace(self, **kw)
+
+
+# torch element type of the colour input for each ges_config.color_storage
+COLOR_DTYPES = {0: torch.float32, 1: torch.float16, 2: torch.bfloat16}
 
 
 def _cam_dict(cam) -> dict:
@@ -351,12 +356,14 @@ class Rasterizer:
 
     # -- calls
     def check_inputs(self, pos_op, lscale_beta, quat, color) -> None:
-        """Shapes the C ABI cannot see behind its pointers."""
+        """Shapes and element types the C ABI cannot see behind its pointers."""
         n, k = self.n, (1 if self.cfg.sh_degree < 0 else (self.cfg.sh_degree + 1) ** 2)
-        for name, t, numel in (("pos_op", pos_op, 4 * n), ("lscale_beta", lscale_beta, 4 * n), ("quat", quat, 4 * n),
-                               ("color", color, 3 * k * n)):
-            if t.dtype != torch.float32 or t.numel() != numel:
-                raise ValueError(f"{name}: expected {numel} float32 values, got {t.numel()} {t.dtype}")
+        cdt = COLOR_DTYPES[self.cfg.color_storage]
+        for name, t, numel, dt in (("pos_op", pos_op, 4 * n, torch.float32),
+                                   ("lscale_beta", lscale_beta, 4 * n, torch.float32),
+                                   ("quat", quat, 4 * n, torch.float32), ("color", color, 3 * k * n, cdt)):
+            if t.dtype != dt or t.numel() != numel:
+                raise ValueError(f"{name}: expected {numel} {dt} values, got {t.numel()} {t.dtype}")
 
     def preprocess(self, pos_op, lscale_beta, quat, color, stream=None) -> None:
         self.check_inputs(pos_op, lscale_beta, quat, color)
@@ -387,7 +394,8 @@ class Rasterizer:
                  stream=None) -> Dict[str, torch.Tensor]:
         if grads is None:
             grads = dict(g_pos_op=torch.empty_like(pos_op), g_lscale_beta=torch.empty_like(lscale_beta),
-                         g_quat=torch.empty_like(quat), g_color=torch.empty_like(color))
+                         g_quat=torch.empty_like(quat),
+                         g_color=torch.empty(color.shape, dtype=torch.float32, device=color.device))
         o = self.out
         ges_render_bwd(self.n, self.n_views, self.cams_c, self.cfg_c, pos_op, lscale_beta, quat, color, self.proj,
                        self.bins, o["color"], o["depth"], o["normal"], o["t_final"], o["last"], g_color, g_depth,

@@ -31,7 +31,8 @@ class GESRasterize(torch.autograd.Function):
         cont = lambda g: None if g is None else g.contiguous()
         grads = rast.backward(pos_op, lscale_beta, quat, color, cont(g_color), cont(g_depth), cont(g_alpha),
                               cont(g_normal))
-        return grads["g_pos_op"], grads["g_lscale_beta"], grads["g_quat"], grads["g_color"], None
+        # the colour gradient is float32; autograd wants the input's element type
+        return grads["g_pos_op"], grads["g_lscale_beta"], grads["g_quat"], grads["g_color"].to(color.dtype), None
 
 
 def rasterize(pos_op, lscale_beta, quat, color, rast: Rasterizer):

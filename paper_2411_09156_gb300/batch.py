@@ -54,7 +54,8 @@ class BatchPlan:
     def _setup(self, capacity: int) -> None:
         self.rast = Rasterizer(self.n, self.cams, self.cfg, capacity=capacity)
         self.capacity = capacity
-        self.grads = {k: torch.empty_like(t) for k, t in
+        # gradients are float32 whatever the colour storage
+        self.grads = {k: torch.empty(t.shape, dtype=torch.float32, device=t.device) for k, t in
                       zip(("g_pos_op", "g_lscale_beta", "g_quat", "g_color"), self.inputs)}
         if self.target is not None:
             r = self.rast

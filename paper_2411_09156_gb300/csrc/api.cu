@@ -30,6 +30,7 @@ bool check_config(const ges_config *cfg) {
     for (int c = 0; c < 3; ++c)
         if (!isfinite(cfg->bg[c])) return false;
     if (cfg->persistent != 0 && cfg->persistent != 1) return false;
+    if (cfg->color_storage < 0 || cfg->color_storage > 2) return false;
     return true;
 }
 
@@ -94,6 +95,7 @@ Params make_params(const ges_config *cfg) {
     P.alpha_max = cfg->alpha_max;
     P.t_min = cfg->t_min;
     for (int c = 0; c < 3; ++c) P.bg[c] = cfg->bg[c];
+    P.color_storage = cfg->color_storage;
     return P;
 }
 
@@ -169,13 +171,13 @@ ges_status ges_get_layout(int32_t n, int32_t n_views, const ges_camera *cams, co
 }
 
 ges_status ges_preprocess(int32_t n, const float *pos_op, const float *lscale_beta, const float *quat,
-                          const float *color, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                          const void *color, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
                           void *proj, size_t proj_bytes, void *stream) {
     if (!check_views(n, n_views, cams, cfg) || !proj || !aligned16(proj)) return GES_ERR_INVALID_ARG;
     const ProjLayout L = proj_layout(n, n_views);
     if (proj_bytes < L.bytes) return GES_ERR_INVALID_ARG;
     if (n > 0 && (!pos_op || !lscale_beta || !quat || !color || !aligned16(pos_op) || !aligned16(lscale_beta) ||
-                  !aligned16(quat)))
+                  !aligned16(quat) || !aligned16(color)))
         return GES_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(proj, 0, 16, s);  // instance total + error word
@@ -313,13 +315,13 @@ ges_status ges_render_bwd_screen(int32_t n, int32_t n_views, const ges_camera *c
 }
 
 ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
-                              const float *pos_op, const float *lscale_beta, const float *quat, const float *color_in,
+                              const float *pos_op, const float *lscale_beta, const float *quat, const void *color_in,
                               const void *proj, size_t proj_bytes, const float *g2d, float *g_pos_op,
                               float *g_lscale_beta, float *g_quat, float *g_color_in, void *stream) {
     if (!check_views(n, n_views, cams, cfg) || !proj) return GES_ERR_INVALID_ARG;
     if (n > 0 && (!pos_op || !lscale_beta || !quat || !color_in || !g_pos_op || !g_lscale_beta || !g_quat ||
                   !g_color_in || !aligned16(pos_op) || !aligned16(lscale_beta) || !aligned16(quat) ||
-                  !aligned16(g_pos_op) || !aligned16(g_lscale_beta) || !aligned16(g_quat)))
+                  !aligned16(color_in) || !aligned16(g_pos_op) || !aligned16(g_lscale_beta) || !aligned16(g_quat)))
         return GES_ERR_INVALID_ARG;
     if (g2d && !aligned16(g2d)) return GES_ERR_INVALID_ARG;
     const ProjLayout PL = proj_layout(n, n_views);
@@ -343,7 +345,7 @@ ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_camera *cams
 }
 
 ges_status ges_render_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
-                          const float *pos_op, const float *lscale_beta, const float *quat, const float *color_in,
+                          const float *pos_op, const float *lscale_beta, const float *quat, const void *color_in,
                           void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes, const float *color,
                           const float *depth, const float *normal, const float *t_final, const uint32_t *last,
                           const float *g_color, const float *g_depth, const float *g_alpha, const float *g_normal,

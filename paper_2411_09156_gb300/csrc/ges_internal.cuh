@@ -2,6 +2,8 @@
 // Nothing here is part of the C ABI (include/ges.h is).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -42,7 +44,30 @@ struct Params {
     int phi_mode;
     float rho, lowpass, alpha_min, alpha_max, t_min;
     float bg[3];
+    int color_storage;  // colour input: 0 float32, 1 binary16, 2 bfloat16
 };
+
+// 16-bit colour value of storage type st (1 binary16, 2 bfloat16) widened to float32 (exact).
+__device__ __forceinline__ float widen16(uint32_t h, int st) {
+    return st == 1 ? __half2float(__ushort_as_half((unsigned short)h)) : __uint_as_float(h << 16);
+}
+
+// Element q of a colour array of storage type st (0 float32, 1 binary16, 2 bfloat16), as float32.
+__device__ __forceinline__ float ld_color(const void *base, int st, size_t q) {
+    if (st == 0) return __ldg(static_cast<const float *>(base) + q);
+    return widen16(__ldg(static_cast<const unsigned short *>(base) + q), st);
+}
+
+// Eight 16-bit colour values at a 16-byte aligned address, widened to float32.
+__device__ __forceinline__ void ld_color8(const void *p, int st, float *out) {
+    const uint4 u = __ldg(static_cast<const uint4 *>(p));
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        out[2 * j] = widen16(w[j] & 0xffffu, st);
+        out[2 * j + 1] = widen16(w[j] >> 16, st);
+    }
+}
 
 // ------------------------------------------------------------------ layouts
 // proj: [header 256 B][records nV x 64 B][binrec nV x 32 B][g2d nV x 64 B]
@@ -319,7 +344,7 @@ __device__ __forceinline__ void set_error(uint32_t *err, uint32_t bit) {
 struct PreArgs {
     int n;
     const float4 *pos_op, *lsb, *quat;
-    const float *color;
+    const void *color;  // Params::color_storage
     float4 *rec;     // [nV][4]
     uint4 *binrec;   // [nV][2]
     unsigned long long *total;
@@ -331,7 +356,7 @@ struct PreArgs {
 struct PreBwdArgs {
     int n;
     const float4 *pos_op, *lsb, *quat;
-    const float *color;
+    const void *color;  // Params::color_storage
     const float4 *rec;
     const float4 *g2d;  // [nV][4]
     float4 *g_pos_op, *g_lsb, *g_quat;

@@ -50,7 +50,7 @@ ges_status accumulator_address(float **out) {
 
 extern "C" ges_status ges_render_bwd_noalloc(
     int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg, const float *pos_op,
-    const float *lscale_beta, const float *quat, const float *color_in, void *proj, size_t proj_bytes,
+    const float *lscale_beta, const float *quat, const void *color_in, void *proj, size_t proj_bytes,
     const void *bins, size_t bins_bytes, const float *color, const float *depth, const float *normal,
     const float *t_final, const uint32_t *last, const float *g_color, const float *g_depth, const float *g_alpha,
     const float *g_normal, float *g_pos_op, float *g_lscale_beta, float *g_quat, float *g_color_in, void *stream) {

@@ -25,16 +25,22 @@ namespace ges {
 // adjacent, so its attributes are fetched from memory once per warp and the
 // records of four splats x eight views are written as eight contiguous runs.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void load_sh_rgb(const float *color, int K, size_t i, const float *Y, float &r, float &g,
-                                            float &b) {
+__device__ __forceinline__ void load_sh_rgb(const void *color, int st, int K, size_t i, const float *Y, float &r,
+                                            float &g, float &b) {
     r = 0.5f; g = 0.5f; b = 0.5f;
     if (K == 16) {
-        const float4 *c4 = reinterpret_cast<const float4 *>(color + i * 48);
         float c[48];
+        if (st == 0) {
+            const float4 *c4 = reinterpret_cast<const float4 *>(static_cast<const float *>(color) + i * 48);
 #pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            const float4 x = __ldg(c4 + q);
-            c[4 * q] = x.x; c[4 * q + 1] = x.y; c[4 * q + 2] = x.z; c[4 * q + 3] = x.w;
+            for (int q = 0; q < 12; ++q) {
+                const float4 x = __ldg(c4 + q);
+                c[4 * q] = x.x; c[4 * q + 1] = x.y; c[4 * q + 2] = x.z; c[4 * q + 3] = x.w;
+            }
+        } else {
+            const char *c16 = static_cast<const char *>(color) + i * 96;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) ld_color8(c16 + 16 * q, st, c + 8 * q);
         }
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
@@ -43,13 +49,13 @@ __device__ __forceinline__ void load_sh_rgb(const float *color, int K, size_t i,
             b = fmaf(c[3 * k + 2], Y[k], b);
         }
     } else {
-        const float *c = color + i * (size_t)K * 3;
+        const size_t base = i * (size_t)K * 3;
 #pragma unroll
         for (int k = 0; k < 16; ++k)
             if (k < K) {
-                r = fmaf(__ldg(c + 3 * k), Y[k], r);
-                g = fmaf(__ldg(c + 3 * k + 1), Y[k], g);
-                b = fmaf(__ldg(c + 3 * k + 2), Y[k], b);
+                r = fmaf(ld_color(color, st, base + 3 * k), Y[k], r);
+                g = fmaf(ld_color(color, st, base + 3 * k + 1), Y[k], g);
+                b = fmaf(ld_color(color, st, base + 3 * k + 2), Y[k], b);
             }
     }
     r = fmaxf(r, 0.f); g = fmaxf(g, 0.f); b = fmaxf(b, 0.f);
@@ -173,11 +179,11 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {
                     dx *= dinv; dy *= dinv; dz *= dinv;
                     float Y[16];
                     sh_eval(a.P.sh_degree, dx, dy, dz, Y);
-                    load_sh_rgb(a.color, a.P.n_coeffs, (size_t)i, Y, rgb0, rgb1, rgb2);
+                    load_sh_rgb(a.color, a.P.color_storage, a.P.n_coeffs, (size_t)i, Y, rgb0, rgb1, rgb2);
                 } else {
-                    rgb0 = __ldg(a.color + 3 * (size_t)i);
-                    rgb1 = __ldg(a.color + 3 * (size_t)i + 1);
-                    rgb2 = __ldg(a.color + 3 * (size_t)i + 2);
+                    rgb0 = ld_color(a.color, a.P.color_storage, 3 * (size_t)i);
+                    rgb1 = ld_color(a.color, a.P.color_storage, 3 * (size_t)i + 1);
+                    rgb2 = ld_color(a.color, a.P.color_storage, 3 * (size_t)i + 2);
                 }
                 // normal: axis of the smallest scale, facing the camera
                 int ks = 0;
@@ -300,12 +306,16 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(PreBwdArgs a) {
         const long long first = gw * spw;
         const int nsp = (int)min((long long)spw, (long long)a.n - first);
         const int nflt = nsp * K * 3;
-        const float *src = a.color + (size_t)first * K * 3;
-        if ((K * 3) % 4 == 0) {
-            const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        const int st = a.P.color_storage;
+        const size_t off = (size_t)first * K * 3;
+        if (st == 0 && (K * 3) % 4 == 0) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(static_cast<const float *>(a.color) + off);
             for (int q = lane; q < nflt / 4; q += 32) reinterpret_cast<float4 *>(wsh)[q] = __ldg(s4 + q);
+        } else if (st != 0 && (K * 3) % 8 == 0) {
+            const char *s16 = static_cast<const char *>(a.color) + 2 * off;
+            for (int q = lane; q < nflt / 8; q += 32) ld_color8(s16 + 16 * q, st, wsh + 8 * q);
         } else {
-            for (int q = lane; q < nflt; q += 32) wsh[q] = __ldg(src + q);
+            for (int q = lane; q < nflt; q += 32) wsh[q] = ld_color(a.color, st, off + q);
         }
         __syncwarp();
     }
