@@ -25,28 +25,41 @@ namespace ges {
 // adjacent, so its attributes are fetched from memory once per warp and the
 // records of four splats x eight views are written as eight contiguous runs.
 // ---------------------------------------------------------------------------
+// Adds value f of a splat's flattened [16][3] coefficients (coefficient f / 3, channel f % 3).
+__device__ __forceinline__ void sh_acc(int f, float x, const float *Y, float &r, float &g, float &b) {
+    const int k = f / 3, ch = f % 3;
+    if (ch == 0) r = fmaf(x, Y[k], r);
+    else if (ch == 1) g = fmaf(x, Y[k], g);
+    else b = fmaf(x, Y[k], b);
+}
+
 __device__ __forceinline__ void load_sh_rgb(const void *color, int st, int K, size_t i, const float *Y, float &r,
                                             float &g, float &b) {
     r = 0.5f; g = 0.5f; b = 0.5f;
     if (K == 16) {
-        float c[48];
+        // each vector load is folded in at once (no 48-value array kept live)
         if (st == 0) {
             const float4 *c4 = reinterpret_cast<const float4 *>(static_cast<const float *>(color) + i * 48);
 #pragma unroll
             for (int q = 0; q < 12; ++q) {
                 const float4 x = __ldg(c4 + q);
-                c[4 * q] = x.x; c[4 * q + 1] = x.y; c[4 * q + 2] = x.z; c[4 * q + 3] = x.w;
+                sh_acc(4 * q, x.x, Y, r, g, b);
+                sh_acc(4 * q + 1, x.y, Y, r, g, b);
+                sh_acc(4 * q + 2, x.z, Y, r, g, b);
+                sh_acc(4 * q + 3, x.w, Y, r, g, b);
             }
         } else {
-            const char *c16 = static_cast<const char *>(color) + i * 96;
+            const uint4 *c16 = reinterpret_cast<const uint4 *>(static_cast<const char *>(color) + i * 96);
 #pragma unroll
-            for (int q = 0; q < 6; ++q) ld_color8(c16 + 16 * q, st, c + 8 * q);
-        }
+            for (int q = 0; q < 6; ++q) {
+                const uint4 u = __ldg(c16 + q);
+                const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            r = fmaf(c[3 * k], Y[k], r);
-            g = fmaf(c[3 * k + 1], Y[k], g);
-            b = fmaf(c[3 * k + 2], Y[k], b);
+                for (int j = 0; j < 4; ++j) {
+                    sh_acc(8 * q + 2 * j, widen16(w[j] & 0xffffu, st), Y, r, g, b);
+                    sh_acc(8 * q + 2 * j + 1, widen16(w[j] >> 16, st), Y, r, g, b);
+                }
+            }
         }
     } else {
         const size_t base = i * (size_t)K * 3;
@@ -77,6 +90,9 @@ __device__ __forceinline__ void warp_tile_tests(const TileJob &J, int lane, int 
                      });
 }
 
+// ST: the colour storage (Params::color_storage), a template parameter so that each storage
+// gets its own register allocation.
+template <int ST>
 __global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {
     const uint32_t NV = (uint32_t)a.V.n_views;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;  // n * NV < 2^31 (host check)
@@ -179,11 +195,11 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {
                     dx *= dinv; dy *= dinv; dz *= dinv;
                     float Y[16];
                     sh_eval(a.P.sh_degree, dx, dy, dz, Y);
-                    load_sh_rgb(a.color, a.P.color_storage, a.P.n_coeffs, (size_t)i, Y, rgb0, rgb1, rgb2);
+                    load_sh_rgb(a.color, ST, a.P.n_coeffs, (size_t)i, Y, rgb0, rgb1, rgb2);
                 } else {
-                    rgb0 = ld_color(a.color, a.P.color_storage, 3 * (size_t)i);
-                    rgb1 = ld_color(a.color, a.P.color_storage, 3 * (size_t)i + 1);
-                    rgb2 = ld_color(a.color, a.P.color_storage, 3 * (size_t)i + 2);
+                    rgb0 = ld_color(a.color, ST, 3 * (size_t)i);
+                    rgb1 = ld_color(a.color, ST, 3 * (size_t)i + 1);
+                    rgb2 = ld_color(a.color, ST, 3 * (size_t)i + 2);
                 }
                 // normal: axis of the smallest scale, facing the camera
                 int ks = 0;
@@ -500,7 +516,10 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(PreBwdArgs a) {
 cudaError_t launch_preprocess(const PreArgs &a, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     const long long threads = (long long)a.n * a.V.n_views;
-    k_preprocess<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+    const unsigned grid = (unsigned)((threads + 255) / 256);
+    if (a.P.color_storage == 1) k_preprocess<1><<<grid, 256, 0, s>>>(a);
+    else if (a.P.color_storage == 2) k_preprocess<2><<<grid, 256, 0, s>>>(a);
+    else k_preprocess<0><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
