@@ -411,13 +411,7 @@ def main():
         d2h = sum(t.numel() * 4 for t in host_out.values())
 
         def e2e_step():
-            for d, h in zip(inputs, host_in):
-                d.copy_(h, non_blocking=True)
-            for d, h in zip(ups, host_up):
-                d.copy_(h, non_blocking=True)
-            g = plan.step()
-            for k in host_out:
-                host_out[k].copy_(g[k], non_blocking=True)
+            plan.step_host(host_in, host_up, host_out)
 
         for _ in range(max(1, args.warmup // 2)):
             e2e_step()

@@ -118,6 +118,37 @@ class BatchPlan:
             events[n].record()
         return self.grads
 
+    def step_host(self, host_inputs: Sequence[torch.Tensor],
+                  host_upstream: Optional[Sequence[Optional[torch.Tensor]]] = None,
+                  host_grads: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
+        """One step whose inputs come from (pinned) host tensors and whose gradients go back to
+        host_grads. The splat parameters are copied first on the current stream; the upstream
+        gradients, which only the render backward reads, are copied on a side stream while
+        preprocess, binning and the forward run, and the backward waits for them."""
+        cur = torch.cuda.current_stream()
+        for d, h in zip(self.inputs, host_inputs):
+            d.copy_(h, non_blocking=True)
+        overlap = host_upstream is not None and self.target is None
+        if overlap:
+            if not hasattr(self, "_side"):
+                self._side = torch.cuda.Stream()
+                self._up_ready = torch.cuda.Event()
+            # after the parameter copies and the previous step's reads of the upstream buffers
+            self._side.wait_stream(cur)
+            with torch.cuda.stream(self._side):
+                for d, h in zip(self.upstream, host_upstream):
+                    if d is not None and h is not None:
+                        d.copy_(h, non_blocking=True)
+            self._up_ready.record(self._side)
+        for k, name in enumerate(self.stages):
+            if overlap and name == "render_bwd":
+                cur.wait_event(self._up_ready)
+            self.run_stage(k)
+        if host_grads is not None:
+            for k, h in host_grads.items():
+                h.copy_(self.grads[k], non_blocking=True)
+        return self.grads
+
     def check(self) -> int:
         """Reads the device error word; on a capacity overflow grows the buffers and re-captures."""
         st = self.rast.sync_status()

@@ -315,3 +315,37 @@ def test_full_size_drt16_3m_batch_sampled_fwd_bwd():
     rows = np.nonzero(np.abs(refg["g_pos_op"]).sum(1) + np.abs(got["g_pos_op"]).sum(1) > 0)[0]
     assert len(rows) > 50
     H.compare_grads(got, refg, rows=rows)
+
+
+def test_step_from_host_buffers_equals_the_device_step():
+    """BatchPlan.step_host (parameters and upstream gradients from pinned host memory, the upstream
+    copy overlapped with the forward on a side stream, gradients copied back) gives the images of
+    the device-resident step bit for bit and its gradients up to the order of the float32 atomics."""
+    from paper_2411_09156_gb300.batch import BatchPlan
+    sc = make_scene(5000, 71, "heightfield", 3)
+    sizes = drt_sizes(160, 104, 4)
+    rng = np.random.default_rng(72)
+    cams = [look_at(5.0 * d / np.linalg.norm(d), (0, 0, 0), w, h) for d, (w, h) in zip(rng.normal(size=(4, 3)), sizes)]
+    cfg = api.GESConfig(sh_degree=3, persistent=1)
+    t = api.scene_tensors(sc)
+    P = sum(w * h for w, h in sizes)
+    g = torch.Generator().manual_seed(5)
+    ups_h = [torch.randn(3 * P, generator=g), torch.randn(P, generator=g), torch.randn(P, generator=g),
+             torch.randn(3 * P, generator=g)]
+    ref_plan = BatchPlan(sc.n, cams, cfg, t, [u.cuda() for u in ups_h])
+    ref = {k: v.clone() for k, v in ref_plan.step().items()}
+    ref_img = ref_plan.rast.out["color"].clone()
+    torch.cuda.synchronize()
+    dev_in = [torch.zeros_like(x) for x in t]
+    plan = BatchPlan(sc.n, cams, cfg, dev_in, [torch.zeros_like(u).cuda() for u in ups_h], capacity=ref_plan.capacity)
+    host_in = [x.cpu().pin_memory() for x in t]
+    host_up = [u.pin_memory() for u in ups_h]
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in ref.items()}
+    for _ in range(2):  # the second step overwrites buffers the first one read
+        plan.step_host(host_in, host_up, host_out)
+        torch.cuda.synchronize()
+        assert plan.check() == 0
+        assert torch.equal(plan.rast.out["color"], ref_img)
+        for k, v in ref.items():
+            a, b = host_out[k].double(), v.cpu().double()
+            assert float((a - b).norm() / b.norm()) <= 1e-4, k
