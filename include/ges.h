@@ -311,6 +311,21 @@ GES_API size_t ges_knn_workspace_bytes(int32_t n);
 GES_API ges_status ges_knn(int32_t n, const float *pos_op, void *workspace, size_t workspace_bytes, int32_t *knn,
                            void *stream);
 
+/* The GES_KNN_K splat centres nearest to each of m arbitrary points, for the density
+ * along a level-set ray (Sec. 3.3, "Mesh Extraction": the start point's 16 closest
+ * splats, as in Sec. 4.2); ges_levelset calls the same search.
+ *   points   [m, 4] float32 (x, y, z, w), 16-byte aligned; w = 0 marks a point without a
+ *            query (its list is all -1)
+ *   knn      [m, 16] int32 (written, 16-byte aligned): point j's neighbours by increasing
+ *            distance, ties to the lower index
+ * The points are searched in grid-cell order; cells are grouped in 2 x 2 x 2 blocks whose
+ * counts let a query in empty space skip them. Exactness and the 65,536-candidate bound
+ * are as for ges_knn. Workspace: ges_knn_points_workspace_bytes(n, m) bytes, 256-byte
+ * aligned, no initialisation needed. n in [16, 2^26], m in [1, 2^28]. */
+GES_API size_t ges_knn_points_workspace_bytes(int32_t n, int32_t m);
+GES_API ges_status ges_knn_points(int32_t n, const float *pos_op, int32_t m, const float *points, void *workspace,
+                                  size_t workspace_bytes, int32_t *knn, void *stream);
+
 /* ---------------------------------------------------------------- GSR point evaluation
  * Generalized surface regularization at m sample points (Sec. 3.3): the density of
  * Eq. 9 over the GES_KNN_K splats nearest to the splat a sample was drawn from, the

@@ -75,6 +75,8 @@ SIGNATURES = {
     "ges_knn_workspace_bytes": (_S, [_I]),
     "ges_knn": (ctypes.c_int, [_I, _P, _P, _S, _P, _P]),
     "ges_gsr_workspace_bytes": (_S, [_I, _I]),
+    "ges_knn_points_workspace_bytes": (_S, [_I, _I]),
+    "ges_knn_points": (ctypes.c_int, [_I, _P, _I, _P, _P, _S, _P, _P]),
     "ges_levelset_workspace_bytes": (_S, [_I, _I]),
     "ges_levelset": (ctypes.c_int, [_I, _P, _P, _P, _CFG, _I, _CAM, _P, _P, _I, _P, _I, ctypes.c_float, _P, _S, _P,
                                     _P]),

@@ -265,6 +265,28 @@ def gsr(pos_op, lscale_beta, quat, knn_idx, sample_splat, sample_z, cfg: Optiona
     return dict(losses=losses, g_pos_op=g[0], g_lscale_beta=g[1], g_quat=g[2], sample_out=so)
 
 
+def ges_knn_points_workspace_bytes(n: int, m: int) -> int:
+    nb = int(_lib.lib().ges_knn_points_workspace_bytes(n, m))
+    if nb == 0:
+        raise ValueError("invalid sizes for ges_knn_points")
+    return nb
+
+
+def ges_knn_points(n, pos_op, m, points, workspace, knn, stream=None) -> None:
+    check(_lib.lib().ges_knn_points(n, _ptr(pos_op), m, _ptr(points), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), _ptr(knn), _stream(stream)),
+          "ges_knn_points")
+
+
+def knn_points(pos_op: torch.Tensor, points: torch.Tensor, stream=None) -> torch.Tensor:
+    """[m, 16] int32: the 16 splat centres nearest to each of the points [m, 4] (w = 0: none, -1)."""
+    n, m = pos_op.shape[0], points.shape[0]
+    ws = torch.empty(ges_knn_points_workspace_bytes(n, m), dtype=torch.uint8, device=pos_op.device)
+    out = torch.empty((m, 16), dtype=torch.int32, device=pos_op.device)
+    ges_knn_points(n, pos_op, m, points, ws, out, stream)
+    return out
+
+
 def ges_levelset_workspace_bytes(n: int, m: int) -> int:
     nb = int(_lib.lib().ges_levelset_workspace_bytes(n, m))
     if nb == 0:

@@ -35,7 +35,7 @@ struct KnnGrid {
 };
 
 struct KnnLayout {
-    uint64_t bbox, grid, keys0, keys1, vals0, vals1, hist, partials, ranges, spos, bytes;
+    uint64_t bbox, grid, keys0, keys1, vals0, vals1, hist, partials, ranges, bcount, spos, bytes;
     uint32_t cap_cells, nblocks;
     int bits;
 };
@@ -61,6 +61,7 @@ KnnLayout knn_layout(int32_t n) {
     L.hist = off; off = al256(off + 4ull * 256 * L.nblocks);
     L.partials = off; off = al256(off + 4ull * (ceil_div_u64(256ull * L.nblocks, kScanTile) + 1));
     L.ranges = off; off = al256(off + 8ull * L.cap_cells);
+    L.bcount = off; off = al256(off + 4ull * L.cap_cells);  // blocks <= cells <= cap_cells
     L.spos = off; off = al256(off + 16ull * n);
     L.bytes = off;
     return L;
@@ -145,7 +146,11 @@ __device__ __forceinline__ int cell_axis(float p, float lo, float inv_h, int dim
     return min(max(c, 0), dim - 1);
 }
 
-__global__ void __launch_bounds__(256) k_knn_keys(const float4 *pos, int n, const KnnGrid *g, uint32_t *keys) {
+// Blocks of 2 x 2 x 2 cells, with their point counts, let point queries skip empty space.
+__device__ __forceinline__ int block_dim(int d) { return (d + 1) >> 1; }
+
+__global__ void __launch_bounds__(256) k_knn_keys(const float4 *pos, int n, const KnnGrid *g, uint32_t *keys,
+                                                  uint32_t *bcount) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 p = __ldg(pos + i);
@@ -154,6 +159,7 @@ __global__ void __launch_bounds__(256) k_knn_keys(const float4 *pos, int n, cons
     const int cy = cell_axis(p.y, G.lo[1], G.inv_h, G.dims[1]);
     const int cz = cell_axis(p.z, G.lo[2], G.inv_h, G.dims[2]);
     keys[i] = (uint32_t)(cx + G.dims[0] * (cy + G.dims[1] * cz));
+    atomicAdd(bcount + ((cx >> 1) + block_dim(G.dims[0]) * ((cy >> 1) + block_dim(G.dims[1]) * (cz >> 1))), 1u);
 }
 
 __global__ void __launch_bounds__(256) k_knn_ranges(const uint32_t *keys, const uint32_t *idx, const float4 *pos,
@@ -171,6 +177,30 @@ __global__ void __launch_bounds__(256) k_knn_ranges(const uint32_t *keys, const 
 __device__ __forceinline__ float dist2(float4 a, float4 b) {
     const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Examines the centres spos[rg.x, rg.y) (at most the rest of the budget) for p's list.
+__device__ __forceinline__ void scan_cell(float4 p, uint2 rg, const float4 *spos, uint32_t &examined, float (&bd)[kK],
+                                          uint32_t (&bi)[kK]) {
+    const uint32_t end = min(rg.y, rg.x + (kQueryBudget - min(examined, kQueryBudget)));
+    examined += rg.y - rg.x;
+    for (uint32_t q = rg.x; q < end; ++q) {
+        const float4 o = __ldg(spos + q);
+        const float d = dist2(p, o);
+        uint32_t id = __float_as_uint(o.w);
+        if (d > bd[kK - 1] || (d == bd[kK - 1] && id >= bi[kK - 1])) continue;
+        float cd = d;
+#pragma unroll
+        for (int k = 0; k < kK; ++k) {  // insert, keeping (distance, index) order
+            const bool less = cd < bd[k] || (cd == bd[k] && id < bi[k]);
+            const float td = bd[k];
+            const uint32_t ti = bi[k];
+            bd[k] = less ? cd : td;
+            bi[k] = less ? id : ti;
+            cd = less ? td : cd;
+            id = less ? ti : id;
+        }
+    }
 }
 
 // Ring search around point p for its kK nearest centres (lists in bd / bi, sorted).
@@ -203,26 +233,7 @@ __device__ __forceinline__ void ring_search(float4 p, const KnnGrid &G, const ui
         auto visit = [&](int cx, int cy, int cz, float gyz) {
             const float gx = gap(0, cx);
             if (fmaf(gx, gx, gyz) > bd[kK - 1]) return;
-            const uint2 rg = __ldg(ranges + (cx + G.dims[0] * (cy + G.dims[1] * cz)));
-            const uint32_t end = min(rg.y, rg.x + (kQueryBudget - min(examined, kQueryBudget)));
-            examined += rg.y - rg.x;
-            for (uint32_t q = rg.x; q < end; ++q) {
-                const float4 o = __ldg(spos + q);
-                const float d = dist2(p, o);
-                uint32_t id = __float_as_uint(o.w);
-                if (d > bd[kK - 1] || (d == bd[kK - 1] && id >= bi[kK - 1])) continue;
-                float cd = d;
-#pragma unroll
-                for (int k = 0; k < kK; ++k) {  // insert, keeping (distance, index) order
-                    const bool less = cd < bd[k] || (cd == bd[k] && id < bi[k]);
-                    const float td = bd[k];
-                    const uint32_t ti = bi[k];
-                    bd[k] = less ? cd : td;
-                    bi[k] = less ? id : ti;
-                    cd = less ? td : cd;
-                    id = less ? ti : id;
-                }
-            }
+            scan_cell(p, __ldg(ranges + (cx + G.dims[0] * (cy + G.dims[1] * cz))), spos, examined, bd, bi);
         };
         // the cells at Chebyshev distance `ring` from the query's cell
         for (int cz = z0; cz <= z1; ++cz) {
@@ -264,6 +275,89 @@ __device__ __forceinline__ void ring_search(float4 p, const KnnGrid &G, const ui
     }
 }
 
+// Distance from p to the slab [lo + i w, lo + (i + 1) w] of one axis, less the slack.
+__device__ __forceinline__ float slab_gap(float lo, float w, float slack, float p, int i) {
+    return fmaxf(fmaxf(lo + (float)i * w - slack - p, p - (lo + (float)(i + 1) * w + slack)), 0.f);
+}
+
+// The same search over Chebyshev rings of 2 x 2 x 2-cell blocks, for queries anywhere in
+// space (start points in front of a surface, rays past its edge): a block whose box lies
+// farther than the 16th candidate, or that holds no centre, costs one test and at most one
+// count read; the cells of the others are pruned and scanned as in ring_search.
+__device__ __forceinline__ void block_search(float4 p, const KnnGrid G, const uint2 *ranges, const uint32_t *bcount,
+                                             const float4 *spos, float (&bd)[kK], uint32_t (&bi)[kK]) {
+    const int dx = G.dims[0], dy = G.dims[1], dz = G.dims[2];
+    const int bx_n = block_dim(dx), by_n = block_dim(dy), bz_n = block_dim(dz);
+    const int cbx = cell_axis(p.x, G.lo[0], G.inv_h, dx) >> 1, cby = cell_axis(p.y, G.lo[1], G.inv_h, dy) >> 1,
+              cbz = cell_axis(p.z, G.lo[2], G.inv_h, dz) >> 1;
+    const float h = G.h, H = G.h + G.h, sl = G.slack;
+    const float lx = G.lo[0], ly = G.lo[1], lz = G.lo[2];
+#pragma unroll
+    for (int k = 0; k < kK; ++k) { bd[k] = __int_as_float(0x7f800000); bi[k] = 0xffffffffu; }
+    // distance from p to the grid's box along each axis
+    const float ox = fmaxf(fmaxf(lx - sl - p.x, p.x - (lx + (float)dx * h + sl)), 0.f);
+    const float oy = fmaxf(fmaxf(ly - sl - p.y, p.y - (ly + (float)dy * h + sl)), 0.f);
+    const float oz = fmaxf(fmaxf(lz - sl - p.z, p.z - (lz + (float)dz * h + sl)), 0.f);
+    const int rmax = max(max(bx_n, by_n), bz_n);
+    uint32_t examined = 0;
+    for (int ring = 0; ring <= rmax && examined < kQueryBudget; ++ring) {
+        const int z0 = max(cbz - ring, 0), z1 = min(cbz + ring, bz_n - 1);
+        const int y0 = max(cby - ring, 0), y1 = min(cby + ring, by_n - 1);
+        const int x0 = max(cbx - ring, 0), x1 = min(cbx + ring, bx_n - 1);
+        auto visit = [&](int bx, int by, int bz, float gyz) {
+            const float gx = slab_gap(lx, H, sl, p.x, bx);
+            if (fmaf(gx, gx, gyz) > bd[kK - 1]) return;
+            if (__ldg(bcount + (bx + bx_n * (by + by_n * bz))) == 0u) return;
+            const int fz1 = min(2 * bz + 1, dz - 1), fy1 = min(2 * by + 1, dy - 1), fx1 = min(2 * bx + 1, dx - 1);
+            for (int fz = 2 * bz; fz <= fz1; ++fz) {
+                const float hz = slab_gap(lz, h, sl, p.z, fz);
+                for (int fy = 2 * by; fy <= fy1; ++fy) {
+                    const float hy = slab_gap(ly, h, sl, p.y, fy);
+                    const float hyz = fmaf(hy, hy, hz * hz);
+                    if (hyz > bd[kK - 1]) continue;
+                    for (int fx = 2 * bx; fx <= fx1; ++fx) {
+                        const float hx = slab_gap(lx, h, sl, p.x, fx);
+                        if (fmaf(hx, hx, hyz) > bd[kK - 1]) continue;
+                        scan_cell(p, __ldg(ranges + (fx + dx * (fy + dy * fz))), spos, examined, bd, bi);
+                    }
+                }
+            }
+        };
+        for (int bz = z0; bz <= z1; ++bz) {
+            const float gz = slab_gap(lz, H, sl, p.z, bz);
+            if (gz * gz > bd[kK - 1]) continue;
+            for (int by = y0; by <= y1; ++by) {
+                const float gy = slab_gap(ly, H, sl, p.y, by);
+                const float gyz = fmaf(gy, gy, gz * gz);
+                if (gyz > bd[kK - 1]) continue;
+                if (abs(bz - cbz) < ring && abs(by - cby) < ring) {  // only the two x faces are new
+                    if (cbx - ring >= 0) visit(cbx - ring, by, bz, gyz);
+                    if (cbx + ring < bx_n) visit(cbx + ring, by, bz, gyz);
+                } else {
+                    for (int bx = x0; bx <= x1; ++bx) visit(bx, by, bz, gyz);
+                }
+            }
+        }
+        // least distance to the grid's box beyond the searched blocks' open faces
+        float b2 = __int_as_float(0x7f800000);
+        bool all = true;
+        auto face = [&](bool open, float g, float o1, float o2) {
+            if (!open) return;
+            g = fmaxf(g - sl, 0.f);
+            b2 = fminf(b2, fmaf(g, g, fmaf(o1, o1, o2 * o2)));
+            all = false;
+        };
+        face(cbx - ring > 0, p.x - (lx + (float)(cbx - ring) * H), oy, oz);
+        face(cbx + ring < bx_n - 1, (lx + (float)(cbx + ring + 1) * H) - p.x, oy, oz);
+        face(cby - ring > 0, p.y - (ly + (float)(cby - ring) * H), ox, oz);
+        face(cby + ring < by_n - 1, (ly + (float)(cby + ring + 1) * H) - p.y, ox, oz);
+        face(cbz - ring > 0, p.z - (lz + (float)(cbz - ring) * H), ox, oy);
+        face(cbz + ring < bz_n - 1, (lz + (float)(cbz + ring + 1) * H) - p.z, ox, oy);
+        if (all) break;
+        if (bi[kK - 1] != 0xffffffffu && bd[kK - 1] <= b2 * (1.f - 1.f / 1048576.f)) break;
+    }
+}
+
 __global__ void __launch_bounds__(128) k_knn_query(const float4 *spos, const uint2 *ranges, const KnnGrid *gp, int n,
                                                    int32_t *knn) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -292,8 +386,9 @@ __global__ void __launch_bounds__(256) k_knn_point_keys(const float4 *pts, int m
 
 // Queries at arbitrary points, taken in cell order (order[r]: the r-th query by cell), so a
 // warp searches one neighbourhood; w = 0: no query, the list is all -1.
-__global__ void __launch_bounds__(128) k_knn_points(const float4 *spos, const uint2 *ranges, const KnnGrid *gp,
-                                                    const float4 *pts, const uint32_t *order, int m, int32_t *knn) {
+__global__ void __launch_bounds__(128) k_knn_points(const float4 *spos, const uint2 *ranges, const uint32_t *bcount,
+                                                    const KnnGrid *gp, const float4 *pts, const uint32_t *order, int m,
+                                                    int32_t *knn) {
     const int r0 = blockIdx.x * blockDim.x + threadIdx.x;
     if (r0 >= m) return;
     const uint32_t r = __ldg(order + r0);
@@ -301,7 +396,8 @@ __global__ void __launch_bounds__(128) k_knn_points(const float4 *spos, const ui
     float bd[kK];
     uint32_t bi[kK];
     if (p.w != 0.f) {
-        ring_search(p, *gp, ranges, spos, bd, bi);
+        const KnnGrid G = *gp;
+        block_search(p, G, ranges, bcount, spos, bd, bi);
     } else {
 #pragma unroll
         for (int k = 0; k < kK; ++k) bi[k] = 0xffffffffu;
@@ -359,12 +455,13 @@ static cudaError_t knn_build(int32_t n, const float4 *pos, void *workspace, cons
     cudaError_t e = cudaMemsetAsync(bb, 0xff, 12, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(bb + 3, 0, 12, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(at<void>(workspace, L.ranges), 0, 8ull * L.cap_cells, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(at<void>(workspace, L.bcount), 0, 4ull * L.cap_cells, s);
     if (e != cudaSuccess) return e;
     k_knn_bbox<<<min(ceil_div_u64(n, 256), 1024u), 256, 0, s>>>(pos, n, bb);
     k_knn_grid<<<1, 1, 0, s>>>(bb, L.cap_cells, grid);
     uint32_t *keys[2] = {at<uint32_t>(workspace, L.keys0), at<uint32_t>(workspace, L.keys1)};
     uint32_t *vals[2] = {at<uint32_t>(workspace, L.vals0), at<uint32_t>(workspace, L.vals1)};
-    k_knn_keys<<<ceil_div_u64(n, 256), 256, 0, s>>>(pos, n, grid, keys[0]);
+    k_knn_keys<<<ceil_div_u64(n, 256), 256, 0, s>>>(pos, n, grid, keys[0], at<uint32_t>(workspace, L.bcount));
     e = radix_sort(keys, vals, true, nullptr, (uint32_t)n, L.bits, at<uint32_t>(workspace, L.hist),
                    at<uint32_t>(workspace, L.partials), s);
     if (e != cudaSuccess) return e;
@@ -398,7 +495,8 @@ cudaError_t knn_points_run(int32_t n, const float4 *pos, int32_t m, const float4
     if (e != cudaSuccess) return e;
     const int res = ((Q.bits + 7) / 8) & 1;
     k_knn_points<<<ceil_div_u64(m, 128), 128, 0, s>>>(at<float4>(workspace, L.spos), at<uint2>(workspace, L.ranges),
-                                                     at<KnnGrid>(workspace, L.grid), pts, vals[res], m, knn);
+                                                     at<uint32_t>(workspace, L.bcount), at<KnnGrid>(workspace, L.grid),
+                                                     pts, vals[res], m, knn);
     return cudaGetLastError();
 }
 
@@ -417,4 +515,23 @@ extern "C" ges_status ges_knn(int32_t n, const float *pos_op, void *workspace, s
     k_knn_query<<<ceil_div_u64(n, 128), 128, 0, s>>>(at<float4>(workspace, L.spos), at<uint2>(workspace, L.ranges),
                                                     at<KnnGrid>(workspace, L.grid), n, knn);
     return cudaGetLastError() == cudaSuccess ? GES_OK : GES_ERR_CUDA;
+}
+
+extern "C" size_t ges_knn_points_workspace_bytes(int32_t n, int32_t m) {
+    if (n < GES_KNN_K || (uint64_t)n > (1ull << 26) || m < 1 || (uint64_t)m > (1ull << 28)) return 0;
+    return knn_points_workspace(n, m);
+}
+
+extern "C" ges_status ges_knn_points(int32_t n, const float *pos_op, int32_t m, const float *points,
+                                     void *workspace, size_t workspace_bytes, int32_t *knn, void *stream) {
+    if (n < GES_KNN_K || (uint64_t)n > (1ull << 26) || m < 1 || (uint64_t)m > (1ull << 28)) return GES_ERR_INVALID_ARG;
+    if (!pos_op || !points || !workspace || !knn) return GES_ERR_INVALID_ARG;
+    if (((uintptr_t)pos_op & 15u) || ((uintptr_t)points & 15u) || ((uintptr_t)workspace & 255u) ||
+        ((uintptr_t)knn & 15u))
+        return GES_ERR_INVALID_ARG;
+    if (workspace_bytes < knn_points_workspace(n, m)) return GES_ERR_INVALID_ARG;
+    return knn_points_run(n, reinterpret_cast<const float4 *>(pos_op), m, reinterpret_cast<const float4 *>(points),
+                          workspace, knn, static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? GES_OK
+               : GES_ERR_CUDA;
 }

@@ -230,7 +230,9 @@ __device__ __forceinline__ float warp_reduce16(float (&g)[16], int lane) {
     return g[0] + __shfl_xor_sync(0xffffffffu, g[0], 1);
 }
 
-template <int TW, int TH>
+// FULL: the depth and normal outputs have upstream gradients too; without them (a loss on the
+// colour, the training step) their channels drop out of the replay.
+template <int TW, int TH, bool FULL>
 __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
     constexpr int NW = TW * TH / 32;
     __shared__ float4 s_rec[NW][32][4];
@@ -271,9 +273,9 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
                 gC0 = a.g_color[c3]; gC1 = a.g_color[c3 + P]; gC2 = a.g_color[c3 + 2 * P];
                 Cf0 = a.color[c3]; Cf1 = a.color[c3 + P]; Cf2 = a.color[c3 + 2 * P];
             }
-            if (a.g_depth) { gD = a.g_depth[g]; Df = a.depth[g]; }
+            if (FULL && a.g_depth) { gD = a.g_depth[g]; Df = a.depth[g]; }
             if (a.g_alpha) gAT = a.g_alpha[g] * a.t_final[g];
-            if (a.g_normal) {
+            if (FULL && a.g_normal) {
                 gN0 = a.g_normal[c3]; gN1 = a.g_normal[c3 + P]; gN2 = a.g_normal[c3 + 2 * P];
                 Nf0 = a.normal[c3]; Nf1 = a.normal[c3 + P]; Nf2 = a.normal[c3 + 2 * P];
             }
@@ -314,16 +316,18 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
                         Ca0 = __fmaf_rn(w, r2.x, Ca0);
                         Ca1 = __fmaf_rn(w, r2.y, Ca1);
                         Ca2 = __fmaf_rn(w, r2.z, Ca2);
-                        Da = __fmaf_rn(w, r2.w, Da);
-                        Na0 = __fmaf_rn(w, r3.x, Na0);
-                        Na1 = __fmaf_rn(w, r3.y, Na1);
-                        Na2 = __fmaf_rn(w, r3.z, Na2);
                         // d out / d alpha_i = T_i sum_k g_k c_ik - (sum_k g_k (F_k - A_k) - g_alpha T_final) / (1 - alpha_i)
-                        const float gc = gC0 * r2.x + gC1 * r2.y + gC2 * r2.z + gD * r2.w + gN0 * r3.x +
-                                         gN1 * r3.y + gN2 * r3.z;
-                        const float behind = gC0 * (Cf0 - Ca0) + gC1 * (Cf1 - Ca1) + gC2 * (Cf2 - Ca2) +
-                                             gD * (Df - Da) + gN0 * (Nf0 - Na0) + gN1 * (Nf1 - Na1) +
-                                             gN2 * (Nf2 - Na2);
+                        float gc = gC0 * r2.x + gC1 * r2.y + gC2 * r2.z;
+                        float behind = gC0 * (Cf0 - Ca0) + gC1 * (Cf1 - Ca1) + gC2 * (Cf2 - Ca2);
+                        if (FULL) {
+                            Da = __fmaf_rn(w, r2.w, Da);
+                            Na0 = __fmaf_rn(w, r3.x, Na0);
+                            Na1 = __fmaf_rn(w, r3.y, Na1);
+                            Na2 = __fmaf_rn(w, r3.z, Na2);
+                            gc = gc + gD * r2.w + gN0 * r3.x + gN1 * r3.y + gN2 * r3.z;
+                            behind = behind + gD * (Df - Da) + gN0 * (Nf0 - Na0) + gN1 * (Nf1 - Na1) +
+                                     gN2 * (Nf2 - Na2);
+                        }
                         const float dal = T * gc - (behind - gAT) * rcp_approx(1.f - al);
                         T = __fmul_rn(T, __fsub_rn(1.f, al));
                         const float o = r1.w, hb = r1.z;
@@ -349,13 +353,15 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
                         g[2] = qx * mx;
                         g[3] = qx * my;
                         g[4] = qy * my;
-                        g[7] = gD * w;
                         g[8] = gC0 * w;
                         g[9] = gC1 * w;
                         g[10] = gC2 * w;
-                        g[12] = gN0 * w;
-                        g[13] = gN1 * w;
-                        g[14] = gN2 * w;
+                        if (FULL) {
+                            g[7] = gD * w;
+                            g[12] = gN0 * w;
+                            g[13] = gN1 * w;
+                            g[14] = gN2 * w;
+                        }
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
@@ -374,23 +380,24 @@ static cudaError_t launch_fwd_t(const FwdArgs &a, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int TW, int TH>
-static cudaError_t launch_bwd_t(const BwdArgs &a, int grid, cudaStream_t s) {
-    k_render_bwd<TW, TH><<<grid, TW * TH, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <int TW, int TH>
-static int persistent_grid(bool bwd, int batch) {
+// Persistent grid: as many CTAs of `kernel` as fit on every SM at once.
+template <class K>
+static int persistent_grid(K kernel, int threads) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (bwd)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_bwd<TW, TH>, TW * TH, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_render_fwd<TW, TH>, TW * TH, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
     if (per < 1) per = 1;
     return sms * per;
+}
+
+template <int TW, int TH, bool FULL>
+static cudaError_t launch_bwd_t(const BwdArgs &a, cudaStream_t s) {
+    int grid = a.V.n_tiles;
+    if (a.queue) grid = min(grid, persistent_grid(k_render_bwd<TW, TH, FULL>, TW * TH));
+    if (grid <= 0) return cudaSuccess;
+    k_render_bwd<TW, TH, FULL><<<grid, TW * TH, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 bool tile_shape_supported(int tw, int th) {
@@ -401,8 +408,8 @@ cudaError_t launch_render_fwd(const FwdArgs &a, cudaStream_t s) {
     const int tw = a.V.tile_w, th = a.V.tile_h;
     int grid = a.V.n_tiles;
     if (a.queue) {
-        grid = (tw == 16) ? persistent_grid<16, 16>(false, a.batch)
-                          : (tw == 8 ? persistent_grid<8, 8>(false, a.batch) : persistent_grid<32, 8>(false, a.batch));
+        grid = (tw == 16) ? persistent_grid(k_render_fwd<16, 16>, 256)
+                          : (tw == 8 ? persistent_grid(k_render_fwd<8, 8>, 64) : persistent_grid(k_render_fwd<32, 8>, 256));
         if (grid > a.V.n_tiles) grid = a.V.n_tiles;
     }
     if (grid <= 0) return cudaSuccess;
@@ -413,16 +420,10 @@ cudaError_t launch_render_fwd(const FwdArgs &a, cudaStream_t s) {
 
 cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s) {
     const int tw = a.V.tile_w, th = a.V.tile_h;
-    int grid = a.V.n_tiles;
-    if (a.queue) {
-        grid = (tw == 16) ? persistent_grid<16, 16>(true, a.batch)
-                          : (tw == 8 ? persistent_grid<8, 8>(true, a.batch) : persistent_grid<32, 8>(true, a.batch));
-        if (grid > a.V.n_tiles) grid = a.V.n_tiles;
-    }
-    if (grid <= 0) return cudaSuccess;
-    if (tw == 16 && th == 16) return launch_bwd_t<16, 16>(a, grid, s);
-    if (tw == 8 && th == 8) return launch_bwd_t<8, 8>(a, grid, s);
-    return launch_bwd_t<32, 8>(a, grid, s);
+    const bool full = a.g_depth != nullptr || a.g_normal != nullptr;
+    if (tw == 16 && th == 16) return full ? launch_bwd_t<16, 16, true>(a, s) : launch_bwd_t<16, 16, false>(a, s);
+    if (tw == 8 && th == 8) return full ? launch_bwd_t<8, 8, true>(a, s) : launch_bwd_t<8, 8, false>(a, s);
+    return full ? launch_bwd_t<32, 8, true>(a, s) : launch_bwd_t<32, 8, false>(a, s);
 }
 
 }  // namespace ges

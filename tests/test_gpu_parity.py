@@ -165,6 +165,32 @@ def test_backward_matches_oracle_gradient(sh_degree):
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-3, c
 
 
+@pytest.mark.parametrize("with_alpha", [False, True])
+def test_backward_colour_only_upstream_matches_oracle(with_alpha):
+    """Upstream gradients on the colour (and the alpha) only, as in the training step: the
+    backward's replay without the depth and normal channels."""
+    sc = make_scene(2000, 32, "object", 3)
+    cams = [look_at((0.5, -2.2, 0.7), (0, 0, 0), 96, 80), look_at((-1.9, 1.2, 0.4), (0, 0, 0), 70, 52)]
+    cfg = api.GESConfig(sh_degree=3, bg=(0.1, 0.2, 0.3))
+    rast, t = H.gpu_forward(sc, cams, cfg)
+    keep = []
+    for v in range(len(cams)):
+        _, ref, _ = H.compare_forward(rast, sc, cams, cfg, v=v)
+        keep.append(H.grad_mask(ref))
+    gc, gd, ga, gn = H.mask_upstream(rast, H.upstream(rast, 2000), keep)
+    ups = (gc, None, ga if with_alpha else None, None)
+    grads = rast.backward(*t, *ups)
+    torch.cuda.synchronize()
+    got = {k: v.double().cpu().numpy() for k, v in grads.items()}
+    refg = None
+    for v in range(len(cams)):
+        oc, _, oa, _ = H.oracle_upstream(rast, (gc, gd, ga, gn), v)
+        z1, z3 = np.zeros_like(oa), np.zeros_like(oc)
+        r = O.backward(sc, cams[v].as_dict(), H.oracle_cfg(cfg), oc, z1, oa if with_alpha else z1, z3)
+        refg = r if refg is None else {k: refg[k] + r[k] for k in refg}
+    H.compare_grads(got, refg)
+
+
 def test_autograd_function_matches_direct_calls():
     from paper_2411_09156_gb300.autograd import rasterize
     sc, cams = _tiny()
