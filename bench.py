@@ -178,6 +178,25 @@ def kernel_source_sha256() -> str:
     return h.hexdigest()
 
 
+def timed_call(fn, warmup: int, steps: int, flush, world: int) -> float:
+    """Mean CUDA-event time (ms) of fn over `steps` calls after `warmup`, L2 flushed before
+    each call, max over ranks."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return max_over_ranks(statistics.mean(ts), world)
+
+
 def levelset_launches(n: int) -> int:
     """Kernels one ges_levelset call launches: start points, splat records, the grid build
     (bounding box, grid, cell keys, ranges, 5 per 8-bit radix pass), the query keys and their
@@ -520,26 +539,11 @@ def main():
         gg = [torch.empty_like(t) for t in inputs[:3]]
         cfg_c = cfg.to_c()
 
-        def timed(fn):
-            for _ in range(args.warmup):
-                fn()
-            torch.cuda.synchronize()
-            ts = []
-            for _ in range(args.steps):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                fn()
-                e1.record()
-                torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            return max_over_ranks(statistics.mean(ts), world)
-
-        knn_ms = timed(lambda: api.ges_knn(n, inputs[0], kws, knn))
-        fwd_ms = timed(lambda: api.ges_gsr(n, inputs[0], inputs[1], inputs[2], cfg_c, knn, n, js, zs, 1.0, 1.0, gws,
-                                            losses))
-        fb_ms = timed(lambda: api.ges_gsr(n, inputs[0], inputs[1], inputs[2], cfg_c, knn, n, js, zs, 1.0, 1.0, gws,
-                                           losses, None, *gg))
+        knn_ms = timed_call(lambda: api.ges_knn(n, inputs[0], kws, knn), args.warmup, args.steps, flush, world)
+        fwd_ms = timed_call(lambda: api.ges_gsr(n, inputs[0], inputs[1], inputs[2], cfg_c, knn, n, js, zs, 1.0, 1.0,
+                                                gws, losses), args.warmup, args.steps, flush, world)
+        fb_ms = timed_call(lambda: api.ges_gsr(n, inputs[0], inputs[1], inputs[2], cfg_c, knn, n, js, zs, 1.0, 1.0,
+                                               gws, losses, None, *gg), args.warmup, args.steps, flush, world)
         gsr = {"value": world * n / (fb_ms / 1e3) / 1e6, "unit": "Msample/s", "samples": n,
                "gsr_fwd_bwd_ms": fb_ms, "gsr_fwd_ms": fwd_ms, "knn_ms": knn_ms,
                "losses": [round(float(x), 6) for x in losses.cpu().tolist()],
@@ -561,8 +565,9 @@ def main():
         pts = torch.empty((P, 8), dtype=torch.float32, device="cuda")
         cams_c = api.cameras_to_c(cams)
         cfg_c = cfg.to_c()
-        ls_ms = timed(lambda: api.ges_levelset(n, inputs[0], inputs[1], inputs[2], cfg_c, len(cams), cams_c,
-                                               o["depth"], o["alpha"], P, pix, 32, 0.3, lws, pts))
+        ls_ms = timed_call(lambda: api.ges_levelset(n, inputs[0], inputs[1], inputs[2], cfg_c, len(cams), cams_c,
+                                                    o["depth"], o["alpha"], P, pix, 32, 0.3, lws, pts),
+                           args.warmup, args.steps, flush, world)
         n_pts = int(pts[:, 7].sum().item())
         levelset = {"value": world * P / (ls_ms / 1e3) / 1e6, "unit": "Mpixel/s", "pixels": P, "points": n_pts,
                     "levelset_ms": ls_ms, "n_steps": 32, "level": 0.3,

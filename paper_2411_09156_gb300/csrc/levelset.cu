@@ -5,10 +5,11 @@
 // by linear interpolation, and the normal grad f / |grad f| there.
 //
 // k_ls_start places x0 (depth D / A along the pixel ray); the KNN point queries of
-// knn.cu (taken in grid-cell order) find the 16 nearest centres; k_ls_march, one thread per pixel, turns each
-// neighbour into the ray form of its axis coordinates, loc_k(t) = loc_k(x0) + t loc_k(v)
-// (shared memory, 8 floats per neighbour), so a step costs three fused multiply-adds
-// per axis and two exponentials per neighbour; the march stops at the first crossing.
+// knn.cu (taken in grid-cell order) find the 16 nearest centres; k_ls_march, one thread per
+// pixel, turns each neighbour into the ray form of its axis coordinates,
+// loc_k(t) = loc_k(x0) + t loc_k(v), so a sample costs three fused multiply-adds per axis and
+// the falloff; densities of 16 samples at a time are held in registers and the march stops
+// after the chunk holding the first crossing.
 #include <cstring>
 
 #include "ges_internal.cuh"
@@ -23,8 +24,8 @@ cudaError_t knn_points_run(int32_t n, const float4 *pos, int32_t m, const float4
 namespace {
 
 constexpr int kK = GES_KNN_K;
-constexpr int kLsThreads = 64;
-constexpr int kCoef = 8;  // per neighbour: loc(x0) (3), loc(v) (3), o, beta/2
+constexpr int kLsThreads = 128;
+constexpr int kLsChunk = 16;  // march samples whose densities a thread holds at once
 constexpr float kHalfLog2e = 0.72134752044448170f;
 
 struct LsArgs {
@@ -87,8 +88,36 @@ __global__ void __launch_bounds__(256) k_ls_prep(LsArgs a) {
     if (i < a.n) build_splat_rec(a.pos_op, a.quat, a.lsb, a.rho, a.phi_mode, i, a.rec);
 }
 
+// Neighbour s of a pixel in ray form: its axis coordinates over s' at x0 (l0) and along the
+// ray direction (lv), so that loc(t) = l0 + t lv; plus opacity and beta / 2.
+struct RayTerm {
+    float l0[3], lv[3], o, hb;
+};
+
+__device__ __forceinline__ RayTerm ray_term(const NbRec &N, float4 p0, const float *dir) {
+    const float dx = p0.x - N.r0.x, dy = p0.y - N.r0.y, dz = p0.z - N.r0.z;
+    RayTerm r;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float is = sqrtf(N.ia[c]);  // 1 / s'
+        r.l0[c] = (N.R[c] * dx + N.R[3 + c] * dy + N.R[6 + c] * dz) * is;
+        r.lv[c] = (N.R[c] * dir[0] + N.R[3 + c] * dir[1] + N.R[6 + c] * dir[2]) * is;
+    }
+    r.o = N.r0.w;
+    r.hb = 0.5f * N.beta;
+    return r;
+}
+
+__device__ __forceinline__ float term_at(const RayTerm &r, float t) {
+    const float l0 = fmaf(t, r.lv[0], r.l0[0]), l1 = fmaf(t, r.lv[1], r.l0[1]), l2 = fmaf(t, r.lv[2], r.l0[2]);
+    const float Q = fmaf(l0, l0, fmaf(l1, l1, l2 * l2));
+    return r.o * exp2f(-kHalfLog2e * exp2f(r.hb * log2f(Q)));
+}
+
+// One thread per pixel. The samples are taken kLsChunk at a time: each neighbour is put in
+// ray form once per chunk and its terms added to the chunk's densities in registers, then
+// the chunk is scanned for the first upward crossing (so nothing is staged in shared memory).
 __global__ void __launch_bounds__(kLsThreads) k_ls_march(LsArgs a) {
-    __shared__ float sc[kK * kCoef * kLsThreads];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.m) return;
     float *o8 = a.out + 8 * (size_t)k;
@@ -98,59 +127,60 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_march(LsArgs a) {
         for (int q = 0; q < 8; ++q) o8[q] = 0.f;
         return;
     }
-    auto S = [&](int s, int f) -> float & { return sc[(s * kCoef + f) * kLsThreads + threadIdx.x]; };
     const int v = a.pixels[2 * (size_t)k], pix = a.pixels[2 * (size_t)k + 1];
     float rc[3], dir[3];
     pixel_ray(a, v, pix, rc, dir);
     const int32_t *nb = a.knn + (size_t)k * kK;
-    // neighbours in ray form; g = the smallest exponent at x0, sigma_g(v)^2 = sum_k (r_k . v)^2 s'_k^2
-    float pmin = __int_as_float(0x7f800000), sig2 = 0.f;
+    int idx[kK];
+#pragma unroll
     for (int s = 0; s < kK; ++s) {
         const int i = __ldg(nb + s);
-        if (i < 0 || i >= a.n) {
-            S(s, 6) = 0.f;  // o = 0: no contribution
-            S(s, 7) = 1.f;
-#pragma unroll
-            for (int f = 0; f < 6; ++f) S(s, f) = 0.f;
-            continue;
-        }
-        const NbRec N = load_rec(a.rec, i);
+        idx[s] = (i >= 0 && i < a.n) ? i : -1;
+    }
+    // g = the smallest exponent at x0, sigma_g(v)^2 = sum_k (r_k . v)^2 s'_k^2
+    float pmin = __int_as_float(0x7f800000), sig2 = 0.f;
+    for (int s = 0; s < kK; ++s) {
+        if (idx[s] < 0) continue;
+        const NbRec N = load_rec(a.rec, idx[s]);
         const float dx = p0.x - N.r0.x, dy = p0.y - N.r0.y, dz = p0.z - N.r0.z;
-        float Q = 0.f, s2 = 0.f;
+        float Q = 0.f, sv = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const float is = sqrtf(N.ia[c]);  // 1 / s'
-            const float pr = N.R[c] * dx + N.R[3 + c] * dy + N.R[6 + c] * dz;
+            const float pr = (N.R[c] * dx + N.R[3 + c] * dy + N.R[6 + c] * dz) * is;
             const float vr = N.R[c] * dir[0] + N.R[3 + c] * dir[1] + N.R[6 + c] * dir[2];
-            S(s, c) = pr * is;
-            S(s, 3 + c) = vr * is;
-            Q = fmaf(pr * is, pr * is, Q);
-            s2 = fmaf(vr * vr, 1.f / N.ia[c], s2);
+            Q = fmaf(pr, pr, Q);
+            sv = fmaf(vr * vr, 1.f / N.ia[c], sv);
         }
-        S(s, 6) = N.r0.w;
-        S(s, 7) = 0.5f * N.beta;
         const float P = exp2f(0.5f * N.beta * log2f(Q));
-        if (P < pmin) { pmin = P; sig2 = s2; }
+        if (P < pmin) { pmin = P; sig2 = sv; }
     }
     const float sigma = sqrtf(sig2);
     const int ns = a.n_steps;
     const float dt = 6.f * sigma / (float)(ns - 1);
     float tprev = 0.f, dprev = 0.f, tstar = 0.f;
     bool found = false;
-    for (int j = 0; j < ns && !found; ++j) {
-        const float t = fmaf((float)j, dt, -3.f * sigma);
-        float d = 0.f;
+    for (int j0 = 0; j0 < ns && !found; j0 += kLsChunk) {
+        float d[kLsChunk];
+#pragma unroll
+        for (int j = 0; j < kLsChunk; ++j) d[j] = 0.f;
         for (int s = 0; s < kK; ++s) {
-            const float l0 = fmaf(t, S(s, 3), S(s, 0)), l1 = fmaf(t, S(s, 4), S(s, 1)), l2 = fmaf(t, S(s, 5), S(s, 2));
-            const float Q = fmaf(l0, l0, fmaf(l1, l1, l2 * l2));
-            d = fmaf(S(s, 6), exp2f(-kHalfLog2e * exp2f(S(s, 7) * log2f(Q))), d);
+            if (idx[s] < 0) continue;
+            const RayTerm r = ray_term(load_rec(a.rec, idx[s]), p0, dir);
+#pragma unroll
+            for (int j = 0; j < kLsChunk; ++j) d[j] += term_at(r, fmaf((float)(j0 + j), dt, -3.f * sigma));
         }
-        if (j > 0 && dprev < a.level && a.level <= d) {
-            tstar = tprev + (a.level - dprev) / (d - dprev) * (t - tprev);
-            found = true;
+#pragma unroll
+        for (int j = 0; j < kLsChunk; ++j) {
+            if (found || j0 + j >= ns) continue;
+            const float t = fmaf((float)(j0 + j), dt, -3.f * sigma);
+            if (j0 + j > 0 && dprev < a.level && a.level <= d[j]) {
+                tstar = tprev + (a.level - dprev) / (d[j] - dprev) * (t - tprev);
+                found = true;
+            }
+            tprev = t;
+            dprev = d[j];
         }
-        tprev = t;
-        dprev = d;
     }
     if (!found) {
 #pragma unroll
@@ -162,20 +192,19 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_march(LsArgs a) {
     float wx = 0.f, wy = 0.f, wz = 0.f;
     float pm = __int_as_float(0x7f800000);
     for (int s = 0; s < kK; ++s) {
-        const int i = __ldg(nb + s);
-        if (i < 0 || i >= a.n) continue;
-        const NbRec N = load_rec(a.rec, i);
-        const float l[3] = {fmaf(tstar, S(s, 3), S(s, 0)), fmaf(tstar, S(s, 4), S(s, 1)),
-                            fmaf(tstar, S(s, 5), S(s, 2))};
+        if (idx[s] < 0) continue;
+        const NbRec N = load_rec(a.rec, idx[s]);
+        const RayTerm r = ray_term(N, p0, dir);
+        const float l[3] = {fmaf(tstar, r.lv[0], r.l0[0]), fmaf(tstar, r.lv[1], r.l0[1]),
+                            fmaf(tstar, r.lv[2], r.l0[2])};
         const float Q = fmaf(l[0], l[0], fmaf(l[1], l[1], l[2] * l[2]));
-        const float hb = S(s, 7);
-        const float P = exp2f(hb * log2f(Q));
+        const float P = exp2f(r.hb * log2f(Q));
         if (P < pm) {
             const float scl = exp2f(-kHalfLog2e * (pm - P));
             if (pm != __int_as_float(0x7f800000)) { wx *= scl; wy *= scl; wz *= scl; }
             pm = P;
         }
-        const float ct = Q > 0.f ? S(s, 6) * exp2f(-kHalfLog2e * (P - pm)) * hb * P / Q : 0.f;
+        const float ct = Q > 0.f ? r.o * exp2f(-kHalfLog2e * (P - pm)) * r.hb * P / Q : 0.f;
         // Sigma^-1 (x - mu) = R diag(1 / s') loc
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
