@@ -108,10 +108,12 @@ __device__ __forceinline__ RayTerm ray_term(const NbRec &N, float4 p0, const flo
     return r;
 }
 
+// o exp(-1/2 Q^(beta/2)) at loc(t), with the hardware base-2 approximations (flushing
+// subnormals: Q below 2^-126 counts as 0, where the term is o).
 __device__ __forceinline__ float term_at(const RayTerm &r, float t) {
     const float l0 = fmaf(t, r.lv[0], r.l0[0]), l1 = fmaf(t, r.lv[1], r.l0[1]), l2 = fmaf(t, r.lv[2], r.l0[2]);
     const float Q = fmaf(l0, l0, fmaf(l1, l1, l2 * l2));
-    return r.o * exp2f(-kHalfLog2e * exp2f(r.hb * log2f(Q)));
+    return r.o * ex2_approx(-kHalfLog2e * ex2_approx(r.hb * lg2_approx(Q)));
 }
 
 // One thread per pixel. The samples are taken kLsChunk at a time: each neighbour is put in
@@ -131,17 +133,17 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_march(LsArgs a) {
     float rc[3], dir[3];
     pixel_ray(a, v, pix, rc, dir);
     const int32_t *nb = a.knn + (size_t)k * kK;
-    int idx[kK];
-#pragma unroll
-    for (int s = 0; s < kK; ++s) {
+    // neighbour s of this pixel, or -1 (lists are re-read from L1 rather than kept in an array)
+    auto nbr = [&](int s) {
         const int i = __ldg(nb + s);
-        idx[s] = (i >= 0 && i < a.n) ? i : -1;
-    }
+        return (i >= 0 && i < a.n) ? i : -1;
+    };
     // g = the smallest exponent at x0, sigma_g(v)^2 = sum_k (r_k . v)^2 s'_k^2
     float pmin = __int_as_float(0x7f800000), sig2 = 0.f;
     for (int s = 0; s < kK; ++s) {
-        if (idx[s] < 0) continue;
-        const NbRec N = load_rec(a.rec, idx[s]);
+        const int i = nbr(s);
+        if (i < 0) continue;
+        const NbRec N = load_rec(a.rec, i);
         const float dx = p0.x - N.r0.x, dy = p0.y - N.r0.y, dz = p0.z - N.r0.z;
         float Q = 0.f, sv = 0.f;
 #pragma unroll
@@ -165,8 +167,9 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_march(LsArgs a) {
 #pragma unroll
         for (int j = 0; j < kLsChunk; ++j) d[j] = 0.f;
         for (int s = 0; s < kK; ++s) {
-            if (idx[s] < 0) continue;
-            const RayTerm r = ray_term(load_rec(a.rec, idx[s]), p0, dir);
+            const int i = nbr(s);
+            if (i < 0) continue;
+            const RayTerm r = ray_term(load_rec(a.rec, i), p0, dir);
 #pragma unroll
             for (int j = 0; j < kLsChunk; ++j) d[j] += term_at(r, fmaf((float)(j0 + j), dt, -3.f * sigma));
         }
@@ -192,8 +195,9 @@ __global__ void __launch_bounds__(kLsThreads) k_ls_march(LsArgs a) {
     float wx = 0.f, wy = 0.f, wz = 0.f;
     float pm = __int_as_float(0x7f800000);
     for (int s = 0; s < kK; ++s) {
-        if (idx[s] < 0) continue;
-        const NbRec N = load_rec(a.rec, idx[s]);
+        const int i = nbr(s);
+        if (i < 0) continue;
+        const NbRec N = load_rec(a.rec, i);
         const RayTerm r = ray_term(N, p0, dir);
         const float l[3] = {fmaf(tstar, r.lv[0], r.l0[0]), fmaf(tstar, r.lv[1], r.l0[1]),
                             fmaf(tstar, r.lv[2], r.l0[2])};
