@@ -140,6 +140,16 @@ GES_API ges_status ges_preprocess(int32_t n, const float *pos_op, const float *l
                           const void *color, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
                           void *proj, size_t proj_bytes, void *stream);
 
+/* ges_preprocess for the splats [first, first + count) of the n only (their entries in
+ * every view; the pointers are those of all n splats). The call whose range starts at 0
+ * clears the instance total and the error word, so it goes first; the ranges of one step
+ * must not overlap and must cover [0, n) before ges_bin. This lets a caller start on the
+ * first splats while the later ones are still being copied to the device. */
+GES_API ges_status ges_preprocess_range(int32_t n, int32_t first, int32_t count, const float *pos_op,
+                                        const float *lscale_beta, const float *quat, const void *color,
+                                        int32_t n_views, const ges_camera *cams, const ges_config *cfg, void *proj,
+                                        size_t proj_bytes, void *stream);
+
 /* Synchronises `stream` and returns in *count the number of tile instances that
  * the last ges_preprocess on `proj` produced (sum of tiles touched). */
 GES_API ges_status ges_instance_count(const void *proj, size_t proj_bytes, uint64_t *count, void *stream);
@@ -214,6 +224,15 @@ GES_API ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_came
                                       const void *color_in, const void *proj, size_t proj_bytes, const float *g2d,
                                       float *g_pos_op, float *g_lscale_beta, float *g_quat, float *g_color_in,
                                       void *stream);
+
+/* ges_preprocess_bwd for the splats [first, first + count) of the n only: their rows of
+ * g_pos_op, g_lscale_beta, g_quat and g_color_in are written, the others left as they are
+ * (so a caller can copy finished rows back to the host while later ranges run). */
+GES_API ges_status ges_preprocess_bwd_range(int32_t n, int32_t first, int32_t count, int32_t n_views,
+                                            const ges_camera *cams, const ges_config *cfg, const float *pos_op,
+                                            const float *lscale_beta, const float *quat, const void *color_in,
+                                            const void *proj, size_t proj_bytes, const float *g2d, float *g_pos_op,
+                                            float *g_lscale_beta, float *g_quat, float *g_color_in, void *stream);
 
 /* ges_render_bwd for callers that cannot allocate device memory.
  *

@@ -59,6 +59,9 @@ SIGNATURES = {
     "ges_bins_bytes": (_S, [_I, _I, _CAM, _CFG, ctypes.c_uint64]),
     "ges_get_layout": (ctypes.c_int, [_I, _I, _CAM, _CFG, ctypes.c_uint64, ctypes.POINTER(Layout)]),
     "ges_preprocess": (ctypes.c_int, [_I, _P, _P, _P, _P, _I, _CAM, _CFG, _P, _S, _P]),
+    "ges_preprocess_range": (ctypes.c_int, [_I, _I, _I, _P, _P, _P, _P, _I, _CAM, _CFG, _P, _S, _P]),
+    "ges_preprocess_bwd_range": (ctypes.c_int, [_I, _I, _I, _I, _CAM, _CFG, _P, _P, _P, _P, _P, _S, _P, _P, _P, _P,
+                                                _P, _P]),
     "ges_instance_count": (ctypes.c_int, [_P, _S, ctypes.POINTER(ctypes.c_uint64), _P]),
     "ges_bin": (ctypes.c_int, [_I, _I, _CAM, _CFG, _P, _S, _P, _S, _P]),
     "ges_render_fwd": (ctypes.c_int, [_I, _I, _CAM, _CFG, _P, _S, _P, _S, _P, _P, _P, _P, _P, _P, _P, _P, _P]),

@@ -117,6 +117,13 @@ def ges_preprocess(n, pos_op, lscale_beta, quat, color, n_views, cams_c, cfg_c, 
           "ges_preprocess")
 
 
+def ges_preprocess_range(n, first, count, pos_op, lscale_beta, quat, color, n_views, cams_c, cfg_c, proj,
+                         stream=None) -> None:
+    check(_lib.lib().ges_preprocess_range(n, first, count, _ptr(pos_op), _ptr(lscale_beta), _ptr(quat), _ptr(color),
+                                          n_views, cams_c, ctypes.byref(cfg_c), _ptr(proj), proj.numel(),
+                                          _stream(stream)), "ges_preprocess_range")
+
+
 def ges_instance_count(proj, stream=None) -> int:
     v = ctypes.c_uint64()
     check(_lib.lib().ges_instance_count(_ptr(proj), proj.numel(), ctypes.byref(v), _stream(stream)),
@@ -151,6 +158,14 @@ def ges_preprocess_bwd(n, n_views, cams_c, cfg_c, pos_op, lscale_beta, quat, col
                                         _ptr(quat), _ptr(color_in), _ptr(proj), proj.numel(), _ptr(g2d),
                                         _ptr(g_pos_op), _ptr(g_lscale_beta), _ptr(g_quat), _ptr(g_color_in),
                                         _stream(stream)), "ges_preprocess_bwd")
+
+
+def ges_preprocess_bwd_range(n, first, count, n_views, cams_c, cfg_c, pos_op, lscale_beta, quat, color_in, proj, g2d,
+                             g_pos_op, g_lscale_beta, g_quat, g_color_in, stream=None) -> None:
+    check(_lib.lib().ges_preprocess_bwd_range(n, first, count, n_views, cams_c, ctypes.byref(cfg_c), _ptr(pos_op),
+                                              _ptr(lscale_beta), _ptr(quat), _ptr(color_in), _ptr(proj), proj.numel(),
+                                              _ptr(g2d), _ptr(g_pos_op), _ptr(g_lscale_beta), _ptr(g_quat),
+                                              _ptr(g_color_in), _stream(stream)), "ges_preprocess_bwd_range")
 
 
 def ges_render_bwd(n, n_views, cams_c, cfg_c, pos_op, lscale_beta, quat, color_in, proj, bins, color, depth, normal,
@@ -392,6 +407,12 @@ class Rasterizer:
         ges_preprocess(self.n, pos_op, lscale_beta, quat, color, self.n_views, self.cams_c, self.cfg_c, self.proj,
                        stream)
 
+    def preprocess_range(self, first: int, count: int, pos_op, lscale_beta, quat, color, stream=None) -> None:
+        """S1-S4 for the splats [first, first + count) (the range from 0 goes first)."""
+        self.check_inputs(pos_op, lscale_beta, quat, color)
+        ges_preprocess_range(self.n, first, count, pos_op, lscale_beta, quat, color, self.n_views, self.cams_c,
+                             self.cfg_c, self.proj, stream)
+
     def bin(self, stream=None) -> None:
         if not self.fixed_capacity:
             m = ges_instance_count(self.proj, stream)
@@ -436,6 +457,15 @@ class Rasterizer:
                        g2d: Optional[torch.Tensor] = None, stream=None) -> Dict[str, torch.Tensor]:
         ges_preprocess_bwd(self.n, self.n_views, self.cams_c, self.cfg_c, pos_op, lscale_beta, quat, color, self.proj,
                            g2d, grads["g_pos_op"], grads["g_lscale_beta"], grads["g_quat"], grads["g_color"], stream)
+        return grads
+
+    def preprocess_bwd_range(self, first: int, count: int, pos_op, lscale_beta, quat, color,
+                             grads: Dict[str, torch.Tensor], g2d: Optional[torch.Tensor] = None,
+                             stream=None) -> Dict[str, torch.Tensor]:
+        """S8 for the splats [first, first + count): only their gradient rows are written."""
+        ges_preprocess_bwd_range(self.n, first, count, self.n_views, self.cams_c, self.cfg_c, pos_op, lscale_beta,
+                                 quat, color, self.proj, g2d, grads["g_pos_op"], grads["g_lscale_beta"],
+                                 grads["g_quat"], grads["g_color"], stream)
         return grads
 
     def sync_status(self, stream=None) -> int:

@@ -67,6 +67,7 @@ class BatchPlan:
                                        device=r.device)
             self.upstream = [self.g_color_loss, None, None, None]
         self.graphs: List[Optional[torch.cuda.CUDAGraph]] = [None] * len(self.stages)
+        self.bin_graph: Optional[torch.cuda.CUDAGraph] = None
         if self.use_graphs:
             self._capture()
 
@@ -99,6 +100,11 @@ class BatchPlan:
             with torch.cuda.graph(g):
                 self._run_stage(k)
             self.graphs[k] = g
+        # binning alone, for steps whose preprocess runs in splat ranges (step_host)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.rast.bin()
+        self.bin_graph = g
         torch.cuda.synchronize()
 
     def run_stage(self, k: int) -> None:
@@ -120,33 +126,58 @@ class BatchPlan:
 
     def step_host(self, host_inputs: Sequence[torch.Tensor],
                   host_upstream: Optional[Sequence[Optional[torch.Tensor]]] = None,
-                  host_grads: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
+                  host_grads: Optional[Dict[str, torch.Tensor]] = None, chunks: int = 4) -> Dict[str, torch.Tensor]:
         """One step whose inputs come from (pinned) host tensors and whose gradients go back to
-        host_grads. The splat parameters are copied first on the current stream; the upstream
-        gradients, which only the render backward reads, are copied on a side stream while
-        preprocess, binning and the forward run, and the backward waits for them."""
+        host_grads. The splat parameters are copied in `chunks` splat ranges on a copy stream,
+        and the preprocess of each range starts as soon as its rows have arrived; the upstream
+        gradients, which only the render backward reads, follow on the same stream while the
+        forward runs; the preprocess backward runs in the same ranges and each range's gradient
+        rows are copied back on a second stream while the next range is computed."""
         cur = torch.cuda.current_stream()
-        for d, h in zip(self.inputs, host_inputs):
-            d.copy_(h, non_blocking=True)
-        overlap = host_upstream is not None and self.target is None
-        if overlap:
-            if not hasattr(self, "_side"):
-                self._side = torch.cuda.Stream()
-                self._up_ready = torch.cuda.Event()
-            # after the parameter copies and the previous step's reads of the upstream buffers
-            self._side.wait_stream(cur)
-            with torch.cuda.stream(self._side):
+        r, x = self.rast, self.inputs
+        n = self.n
+        chunks = max(1, min(int(chunks), n)) if n > 0 else 1
+        bounds = [(n * c // chunks, n * (c + 1) // chunks) for c in range(chunks)]
+        if not hasattr(self, "_h2d"):
+            self._h2d, self._d2h = torch.cuda.Stream(), torch.cuda.Stream()
+            self._up_ready = torch.cuda.Event()
+        ev_in = [torch.cuda.Event() for _ in bounds]
+        # the copies wait for the previous step, which still reads the device inputs
+        self._h2d.wait_stream(cur)
+        with torch.cuda.stream(self._h2d):
+            for c, (a, b) in enumerate(bounds):
+                for d, h in zip(x, host_inputs):
+                    d[a:b].copy_(h[a:b], non_blocking=True)
+                ev_in[c].record()
+            overlap = host_upstream is not None and self.target is None
+            if overlap:
                 for d, h in zip(self.upstream, host_upstream):
                     if d is not None and h is not None:
                         d.copy_(h, non_blocking=True)
-            self._up_ready.record(self._side)
+                self._up_ready.record()
+        for c, (a, b) in enumerate(bounds):
+            cur.wait_event(ev_in[c])
+            r.preprocess_range(a, b - a, *x)
+        if self.bin_graph is not None:
+            self.bin_graph.replay()
+        else:
+            r.bin()
         for k, name in enumerate(self.stages):
-            if overlap and name == "render_bwd":
+            if name in ("preprocess_bin", "preprocess_bwd"):
+                continue
+            if name == "render_bwd" and overlap:
                 cur.wait_event(self._up_ready)
             self.run_stage(k)
-        if host_grads is not None:
-            for k, h in host_grads.items():
-                h.copy_(self.grads[k], non_blocking=True)
+        for c, (a, b) in enumerate(bounds):
+            r.preprocess_bwd_range(a, b - a, *x, self.grads)
+            if host_grads is not None:
+                done = torch.cuda.Event()
+                done.record(cur)
+                self._d2h.wait_event(done)
+                with torch.cuda.stream(self._d2h):
+                    for k, h in host_grads.items():
+                        h[a:b].copy_(self.grads[k][a:b], non_blocking=True)
+        cur.wait_stream(self._d2h)
         return self.grads
 
     def check(self) -> int:

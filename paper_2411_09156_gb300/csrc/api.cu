@@ -170,20 +170,24 @@ ges_status ges_get_layout(int32_t n, int32_t n_views, const ges_camera *cams, co
     return GES_OK;
 }
 
-ges_status ges_preprocess(int32_t n, const float *pos_op, const float *lscale_beta, const float *quat,
-                          const void *color, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
-                          void *proj, size_t proj_bytes, void *stream) {
+// S1-S4 for the splats [first, first + count) of n; the range starting at 0 clears the header.
+static ges_status preprocess_impl(int32_t n, int32_t first, int32_t count, const float *pos_op,
+                                  const float *lscale_beta, const float *quat, const void *color, int32_t n_views,
+                                  const ges_camera *cams, const ges_config *cfg, void *proj, size_t proj_bytes,
+                                  void *stream) {
     if (!check_views(n, n_views, cams, cfg) || !proj || !aligned16(proj)) return GES_ERR_INVALID_ARG;
+    if (first < 0 || count < 0 || (int64_t)first + count > n) return GES_ERR_INVALID_ARG;
     const ProjLayout L = proj_layout(n, n_views);
     if (proj_bytes < L.bytes) return GES_ERR_INVALID_ARG;
     if (n > 0 && (!pos_op || !lscale_beta || !quat || !color || !aligned16(pos_op) || !aligned16(lscale_beta) ||
                   !aligned16(quat) || !aligned16(color)))
         return GES_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(proj, 0, 16, s);  // instance total + error word
-    if (e != cudaSuccess) return GES_ERR_CUDA;
+    if (first == 0 && cudaMemsetAsync(proj, 0, 16, s) != cudaSuccess) return GES_ERR_CUDA;  // total + error word
     PreArgs a;
     a.n = n;
+    a.first = first;
+    a.count = count;
     a.pos_op = reinterpret_cast<const float4 *>(pos_op);
     a.lsb = reinterpret_cast<const float4 *>(lscale_beta);
     a.quat = reinterpret_cast<const float4 *>(quat);
@@ -195,6 +199,20 @@ ges_status ges_preprocess(int32_t n, const float *pos_op, const float *lscale_be
     a.P = make_params(cfg);
     a.V = make_views(n_views, cams, cfg);
     return cuda_status(launch_preprocess(a, s));
+}
+
+ges_status ges_preprocess(int32_t n, const float *pos_op, const float *lscale_beta, const float *quat,
+                          const void *color, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                          void *proj, size_t proj_bytes, void *stream) {
+    return preprocess_impl(n, 0, n, pos_op, lscale_beta, quat, color, n_views, cams, cfg, proj, proj_bytes, stream);
+}
+
+ges_status ges_preprocess_range(int32_t n, int32_t first, int32_t count, const float *pos_op,
+                                const float *lscale_beta, const float *quat, const void *color, int32_t n_views,
+                                const ges_camera *cams, const ges_config *cfg, void *proj, size_t proj_bytes,
+                                void *stream) {
+    return preprocess_impl(n, first, count, pos_op, lscale_beta, quat, color, n_views, cams, cfg, proj, proj_bytes,
+                           stream);
 }
 
 ges_status ges_instance_count(const void *proj, size_t proj_bytes, uint64_t *count, void *stream) {
@@ -314,11 +332,14 @@ ges_status ges_render_bwd_screen(int32_t n, int32_t n_views, const ges_camera *c
     return cuda_status(launch_render_bwd(b, s));
 }
 
-ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
-                              const float *pos_op, const float *lscale_beta, const float *quat, const void *color_in,
-                              const void *proj, size_t proj_bytes, const float *g2d, float *g_pos_op,
-                              float *g_lscale_beta, float *g_quat, float *g_color_in, void *stream) {
+// S8 for the splats [first, first + count) of n.
+static ges_status preprocess_bwd_impl(int32_t n, int32_t first, int32_t count, int32_t n_views,
+                                      const ges_camera *cams, const ges_config *cfg, const float *pos_op,
+                                      const float *lscale_beta, const float *quat, const void *color_in,
+                                      const void *proj, size_t proj_bytes, const float *g2d, float *g_pos_op,
+                                      float *g_lscale_beta, float *g_quat, float *g_color_in, void *stream) {
     if (!check_views(n, n_views, cams, cfg) || !proj) return GES_ERR_INVALID_ARG;
+    if (first < 0 || count < 0 || (int64_t)first + count > n) return GES_ERR_INVALID_ARG;
     if (n > 0 && (!pos_op || !lscale_beta || !quat || !color_in || !g_pos_op || !g_lscale_beta || !g_quat ||
                   !g_color_in || !aligned16(pos_op) || !aligned16(lscale_beta) || !aligned16(quat) ||
                   !aligned16(color_in) || !aligned16(g_pos_op) || !aligned16(g_lscale_beta) || !aligned16(g_quat)))
@@ -329,6 +350,8 @@ ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_camera *cams
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     PreBwdArgs p;
     p.n = n;
+    p.first = first;
+    p.count = count;
     p.pos_op = reinterpret_cast<const float4 *>(pos_op);
     p.lsb = reinterpret_cast<const float4 *>(lscale_beta);
     p.quat = reinterpret_cast<const float4 *>(quat);
@@ -342,6 +365,23 @@ ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_camera *cams
     p.P = make_params(cfg);
     p.V = make_views(n_views, cams, cfg);
     return cuda_status(launch_preprocess_bwd(p, s));
+}
+
+ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
+                              const float *pos_op, const float *lscale_beta, const float *quat, const void *color_in,
+                              const void *proj, size_t proj_bytes, const float *g2d, float *g_pos_op,
+                              float *g_lscale_beta, float *g_quat, float *g_color_in, void *stream) {
+    return preprocess_bwd_impl(n, 0, n, n_views, cams, cfg, pos_op, lscale_beta, quat, color_in, proj, proj_bytes,
+                               g2d, g_pos_op, g_lscale_beta, g_quat, g_color_in, stream);
+}
+
+ges_status ges_preprocess_bwd_range(int32_t n, int32_t first, int32_t count, int32_t n_views,
+                                    const ges_camera *cams, const ges_config *cfg, const float *pos_op,
+                                    const float *lscale_beta, const float *quat, const void *color_in,
+                                    const void *proj, size_t proj_bytes, const float *g2d, float *g_pos_op,
+                                    float *g_lscale_beta, float *g_quat, float *g_color_in, void *stream) {
+    return preprocess_bwd_impl(n, first, count, n_views, cams, cfg, pos_op, lscale_beta, quat, color_in, proj,
+                               proj_bytes, g2d, g_pos_op, g_lscale_beta, g_quat, g_color_in, stream);
 }
 
 ges_status ges_render_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,

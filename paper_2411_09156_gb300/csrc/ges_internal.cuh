@@ -343,6 +343,7 @@ __device__ __forceinline__ void set_error(uint32_t *err, uint32_t bit) {
 // ------------------------------------------------------------------ kernel arguments
 struct PreArgs {
     int n;
+    int first, count;  // the splats [first, first + count) of the n
     const float4 *pos_op, *lsb, *quat;
     const void *color;  // Params::color_storage
     float4 *rec;     // [nV][4]
@@ -355,6 +356,7 @@ struct PreArgs {
 
 struct PreBwdArgs {
     int n;
+    int first, count;  // the splats [first, first + count) of the n
     const float4 *pos_op, *lsb, *quat;
     const void *color;  // Params::color_storage
     const float4 *rec;

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {
     const uint32_t NV = (uint32_t)a.V.n_views;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;  // n * NV < 2^31 (host check)
     const int lane = threadIdx.x & 31;
-    const bool live = t < (uint32_t)a.n * NV;
+    const bool live = t < (uint32_t)a.count * NV;
     const int tw = a.V.tile_w, th = a.V.tile_h;
     const int lw = __ffs(tw) - 1, lh = __ffs(th) - 1;  // tile sides are powers of two
     uint32_t i = 0, v = 0;
@@ -107,8 +107,9 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {
     TileJob J = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, 0u};
     uint32_t rect = 0, rdim = 0;
     if (live) {
-        i = t / NV;
-        v = t - i * NV;
+        const uint32_t il = t / NV;
+        v = t - il * NV;
+        i = (uint32_t)a.first + il;
         e = (size_t)v * a.n + i;
         const float4 po = __ldg(a.pos_op + i);
         const float4 ls = __ldg(a.lsb + i);
@@ -308,10 +309,11 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(PreBwdArgs a) {
     const int spw = 32 / seg;  // splats per warp
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int v = lane % seg;
-    const long long il = gw * spw + lane / seg;
-    if (gw * spw >= a.n) return;  // whole warp past the end (warp-uniform)
-    const bool splat_ok = il < a.n;
-    const int i = splat_ok ? (int)il : a.n - 1;
+    const long long end = (long long)a.first + a.count;
+    const long long il = a.first + gw * spw + lane / seg;
+    if (gw * spw >= a.count) return;  // whole warp past the end (warp-uniform)
+    const bool splat_ok = il < end;
+    const int i = splat_ok ? (int)il : (int)(end - 1);
     const bool active = splat_ok && v < NV;
     // the SH coefficients of the warp's splats, loaded once with coalesced float4 reads
     // (dynamic shared memory: spw * K * 3 floats per warp)
@@ -319,8 +321,8 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(PreBwdArgs a) {
     const int K = a.P.n_coeffs;
     float *wsh = s_sh + (threadIdx.x >> 5) * (spw * K * 3);
     if (a.P.sh_degree >= 0) {
-        const long long first = gw * spw;
-        const int nsp = (int)min((long long)spw, (long long)a.n - first);
+        const long long first = a.first + gw * spw;
+        const int nsp = (int)min((long long)spw, end - first);
         const int nflt = nsp * K * 3;
         const int st = a.P.color_storage;
         const size_t off = (size_t)first * K * 3;
@@ -514,8 +516,8 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(PreBwdArgs a) {
 }
 
 cudaError_t launch_preprocess(const PreArgs &a, cudaStream_t s) {
-    if (a.n <= 0) return cudaSuccess;
-    const long long threads = (long long)a.n * a.V.n_views;
+    if (a.count <= 0) return cudaSuccess;
+    const long long threads = (long long)a.count * a.V.n_views;
     const unsigned grid = (unsigned)((threads + 255) / 256);
     if (a.P.color_storage == 1) k_preprocess<1><<<grid, 256, 0, s>>>(a);
     else if (a.P.color_storage == 2) k_preprocess<2><<<grid, 256, 0, s>>>(a);
@@ -524,10 +526,10 @@ cudaError_t launch_preprocess(const PreArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t s) {
-    if (a.n <= 0) return cudaSuccess;
+    if (a.count <= 0) return cudaSuccess;
     int seg = 1;
     while (seg < a.V.n_views) seg <<= 1;
-    const long long warps = ((long long)a.n + (32 / seg) - 1) / (32 / seg);
+    const long long warps = ((long long)a.count + (32 / seg) - 1) / (32 / seg);
     const size_t smem = a.P.sh_degree >= 0 ? (size_t)8 * (32 / seg) * a.P.n_coeffs * 3 * sizeof(float) : 0;
     const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
     switch (seg) {

@@ -344,9 +344,11 @@ def test_full_size_drt16_3m_batch_sampled_fwd_bwd():
 
 
 def test_step_from_host_buffers_equals_the_device_step():
-    """BatchPlan.step_host (parameters and upstream gradients from pinned host memory, the upstream
-    copy overlapped with the forward on a side stream, gradients copied back) gives the images of
-    the device-resident step bit for bit and its gradients up to the order of the float32 atomics."""
+    """BatchPlan.step_host (parameters copied from pinned host memory in splat ranges, each
+    range's preprocess started on arrival, the upstream copy overlapped with the forward, the
+    preprocess backward in ranges with their gradient rows copied back as they finish) gives
+    the images of the device-resident step bit for bit and its gradients up to the order of
+    the float32 atomics, for 1, 3 and 4 ranges."""
     from paper_2411_09156_gb300.batch import BatchPlan
     sc = make_scene(5000, 71, "heightfield", 3)
     sizes = drt_sizes(160, 104, 4)
@@ -367,8 +369,8 @@ def test_step_from_host_buffers_equals_the_device_step():
     host_in = [x.cpu().pin_memory() for x in t]
     host_up = [u.pin_memory() for u in ups_h]
     host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in ref.items()}
-    for _ in range(2):  # the second step overwrites buffers the first one read
-        plan.step_host(host_in, host_up, host_out)
+    for chunks in (1, 3, 4):  # later steps overwrite buffers the earlier ones read
+        plan.step_host(host_in, host_up, host_out, chunks=chunks)
         torch.cuda.synchronize()
         assert plan.check() == 0
         assert torch.equal(plan.rast.out["color"], ref_img)
