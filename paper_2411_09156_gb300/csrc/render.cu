@@ -401,21 +401,23 @@ static cudaError_t launch_bwd_t(const BwdArgs &a, cudaStream_t s) {
 }
 
 bool tile_shape_supported(int tw, int th) {
-    return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
+    return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8) || (tw == 8 && th == 32);
+}
+
+template <int TW, int TH>
+static cudaError_t launch_fwd_shape(const FwdArgs &a, cudaStream_t s) {
+    int grid = a.V.n_tiles;
+    if (a.queue) grid = min(grid, persistent_grid(k_render_fwd<TW, TH>, TW * TH));
+    if (grid <= 0) return cudaSuccess;
+    return launch_fwd_t<TW, TH>(a, grid, s);
 }
 
 cudaError_t launch_render_fwd(const FwdArgs &a, cudaStream_t s) {
     const int tw = a.V.tile_w, th = a.V.tile_h;
-    int grid = a.V.n_tiles;
-    if (a.queue) {
-        grid = (tw == 16) ? persistent_grid(k_render_fwd<16, 16>, 256)
-                          : (tw == 8 ? persistent_grid(k_render_fwd<8, 8>, 64) : persistent_grid(k_render_fwd<32, 8>, 256));
-        if (grid > a.V.n_tiles) grid = a.V.n_tiles;
-    }
-    if (grid <= 0) return cudaSuccess;
-    if (tw == 16 && th == 16) return launch_fwd_t<16, 16>(a, grid, s);
-    if (tw == 8 && th == 8) return launch_fwd_t<8, 8>(a, grid, s);
-    return launch_fwd_t<32, 8>(a, grid, s);
+    if (tw == 16 && th == 16) return launch_fwd_shape<16, 16>(a, s);
+    if (tw == 8 && th == 8) return launch_fwd_shape<8, 8>(a, s);
+    if (tw == 8 && th == 32) return launch_fwd_shape<8, 32>(a, s);
+    return launch_fwd_shape<32, 8>(a, s);
 }
 
 cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s) {
@@ -423,6 +425,7 @@ cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s) {
     const bool full = a.g_depth != nullptr || a.g_normal != nullptr;
     if (tw == 16 && th == 16) return full ? launch_bwd_t<16, 16, true>(a, s) : launch_bwd_t<16, 16, false>(a, s);
     if (tw == 8 && th == 8) return full ? launch_bwd_t<8, 8, true>(a, s) : launch_bwd_t<8, 8, false>(a, s);
+    if (tw == 8 && th == 32) return full ? launch_bwd_t<8, 32, true>(a, s) : launch_bwd_t<8, 32, false>(a, s);
     return full ? launch_bwd_t<32, 8, true>(a, s) : launch_bwd_t<32, 8, false>(a, s);
 }
 
