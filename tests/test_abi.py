@@ -93,7 +93,8 @@ def test_invalid_arguments_are_rejected_on_the_host():
     lib = _lib.lib()
     cams = _cams([(64, 64)])
     bad = [api.GESConfig(tile_w=12), api.GESConfig(batch=100), api.GESConfig(sh_degree=4),
-           api.GESConfig(alpha_min=0.0), api.GESConfig(alpha_max=1.0), api.GESConfig(phi_mode=3)]
+           api.GESConfig(alpha_min=0.0), api.GESConfig(alpha_max=1.0), api.GESConfig(phi_mode=3),
+           api.GESConfig(color_storage=3), api.GESConfig(tile_w=32, tile_h=32)]
     for cfg in bad:
         assert api.ges_bins_bytes(10, 1, cams, cfg.to_c(), 100) == 0
         st = lib.ges_preprocess(10, 16, 16, 16, 16, 1, cams, ctypes.byref(cfg.to_c()), 256, 1 << 20, None)
@@ -105,6 +106,13 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert lib.ges_preprocess(10, 16, 16, 16, 16, 1, cams, ctypes.byref(ok), 256, 100, None) == 1
     assert lib.ges_preprocess(10, None, 16, 16, 16, 1, cams, ctypes.byref(ok), 256, 1 << 20, None) == 1
     assert lib.ges_bin(10, 1, cams, ctypes.byref(ok), 256, 1 << 20, 256, 10, None) == 1
+    # a colour pointer off the 16-byte grid; splat ranges outside [0, n)
+    assert lib.ges_preprocess(10, 16, 16, 16, 24, 1, cams, ctypes.byref(ok), 256, 1 << 20, None) == 1
+    for first, count in ((-1, 5), (6, 5), (0, 11), (3, -1)):
+        assert lib.ges_preprocess_range(10, first, count, 16, 16, 16, 16, 1, cams, ctypes.byref(ok), 256, 1 << 20,
+                                        None) == 1
+        assert lib.ges_preprocess_bwd_range(10, first, count, 1, cams, ctypes.byref(ok), 16, 16, 16, 16, 256,
+                                            1 << 20, None, 16, 16, 16, 16, None) == 1
     badcam = _cams([(0, 64)])
     assert api.ges_bins_bytes(10, 1, badcam, ok, 100) == 0
     assert api.ges_proj_bytes(-1, 1) == 0 and api.ges_proj_bytes(10, 0) == 0
