@@ -126,7 +126,7 @@ class BatchPlan:
 
     def step_host(self, host_inputs: Sequence[torch.Tensor],
                   host_upstream: Optional[Sequence[Optional[torch.Tensor]]] = None,
-                  host_grads: Optional[Dict[str, torch.Tensor]] = None, chunks: int = 4) -> Dict[str, torch.Tensor]:
+                  host_grads: Optional[Dict[str, torch.Tensor]] = None, chunks: int = 8) -> Dict[str, torch.Tensor]:
         """One step whose inputs come from (pinned) host tensors and whose gradients go back to
         host_grads. The splat parameters are copied in `chunks` splat ranges on a copy stream,
         and the preprocess of each range starts as soon as its rows have arrived; the upstream
