@@ -1,6 +1,7 @@
 """Pins of the level-set extraction oracle (oracle/levelset.py): the ray and its start point
 against the camera projection, the crossing of an isolated flat splat against its closed form,
-its normal, sigma_g(v) along a principal axis, and the cases without a point."""
+its normal, sigma_g(v) along a principal axis, the cases without a point, the normal against
+central differences of the density, and the choice of the rising crossing."""
 import numpy as np
 from scipy.spatial.transform import Rotation
 
@@ -72,3 +73,45 @@ def test_no_point_without_coverage_or_crossing():
     cam = _cam(w=64, h=64)
     assert not OLS.extract(pos, lsb, q, cam, depth=4.0, alpha=1.0, px=32, py=32)["valid"]
     assert not OLS.extract(pos, lsb, q, cam, depth=4.0, alpha=5e-5, px=32, py=32)["valid"]
+
+
+def test_normal_is_the_finite_difference_gradient_of_the_density():
+    # several overlapping rotated splats of different beta: -grad d by central differences of
+    # density_at must have the direction normal_at reports, anywhere (not only on the level set)
+    rng = np.random.default_rng(4)
+    n = 17
+    pos = np.concatenate([rng.normal(0, 0.05, (n, 3)), rng.uniform(0.3, 1.0, (n, 1))], 1)
+    lsb = np.concatenate([rng.normal(-2.5, 0.3, (n, 3)), rng.uniform(1.2, 5.0, (n, 1))], 1)
+    q = Rotation.random(n, random_state=5).as_quat()[:, [3, 0, 1, 2]]
+    nb = np.arange(16)
+    for x in rng.normal(0, 0.08, (6, 3)):
+        h = 1e-6
+        grad = np.array([(OLS.density_at(pos, lsb, q, nb, x + h * e) - OLS.density_at(pos, lsb, q, nb, x - h * e))
+                         / (2 * h) for e in np.eye(3)])
+        nrm, cond = OLS.normal_at(pos, lsb, q, nb, x)
+        np.testing.assert_allclose(nrm, -grad / np.linalg.norm(grad), atol=1e-6)
+        assert cond >= 1.0
+
+
+def test_first_crossing_from_the_camera_side():
+    # a flat splat facing the camera on its axis at z = -0.2 (another far behind it, at z = +0.2):
+    # d rises through the level in front of the near splat and falls through it again behind;
+    # the point is the rising crossing, on the camera side
+    s = 0.01
+    pos = np.zeros((18, 4))
+    pos[0, :3], pos[0, 3] = [0.0, 0.0, -0.2], 0.9
+    pos[1, :3], pos[1, 3] = [0.0, 0.0, 0.2], 0.9
+    pos[2:, :3] = 100.0 + np.arange(16)[:, None]
+    lsb = np.zeros((18, 4))
+    lsb[:, :3] = [np.log(0.5), np.log(0.5), np.log(s)]
+    lsb[:, 3] = 2.0
+    q = np.tile([1.0, 0, 0, 0], (18, 1))
+    cam = _cam(w=64, h=64)
+    # start just behind the near splat (camera depth 4 is z = 0): sigma_g along the axis is s, so
+    # +-3 sigma covers both of its crossings
+    out = OLS.extract(pos, lsb, q, cam, depth=3.8 + 0.5 * s, alpha=1.0, px=32, py=32, n_steps=2001, phi_mode=0)
+    assert out["valid"]
+    z = out["point"][2]
+    assert -0.2 - 4 * s < z < -0.2, z  # on the camera side of the near splat
+    d = OLS.density_at(pos, lsb, q, out["neighbours"], out["point"], phi_mode=0)
+    assert abs(d - 0.3) < 1e-3
