@@ -195,7 +195,8 @@ GES_API ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *
  * layouts as the outputs; any of g_color, g_depth, g_alpha, g_normal may be NULL
  * for zero). Outputs g_pos_op, g_lscale_beta, g_quat, g_color_in have the input
  * layouts (g_color_in in float32 whatever cfg->color_storage) and are OVERWRITTEN
- * (summed over views). g2d may be NULL, else it
+ * (summed over views). Without g_depth and g_normal (a loss on the colour, as in
+ * training) the replay leaves out the depth and normal channels, which is faster. g2d may be NULL, else it
  * receives the per-entry screen-space gradients [n_views * n, 16]. */
 GES_API ges_status ges_render_bwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
                           const float *pos_op, const float *lscale_beta, const float *quat, const void *color_in,
