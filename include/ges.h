@@ -11,7 +11,11 @@
  * and composited front to back, the discrete form of the volume rendering
  * integral of Eq. 5, into colour, depth (Sec. 3.3, the depth map that mesh
  * extraction samples), alpha, and the normal n_g* of the flattened splats
- * (Sec. 3.3, Eq. 10-13).
+ * (Sec. 3.3, Eq. 10-13). Beside the rasterizer: the reconstruction loss of Eq. 8
+ * and its gradient (ges_loss_rgb), the 16-nearest-neighbour lists and the
+ * generalized surface regularization of Eq. 9-13 at sample points (ges_knn,
+ * ges_gsr), and the level-set points and normals of the mesh extraction of
+ * Sec. 3.3 (ges_knn_points, ges_levelset).
  *
  * Conventions
  *  - Every pointer argument except `cams`, `cfg` and `count` is a DEVICE
@@ -25,13 +29,13 @@
  *    returns GES_ERR_CUDA. Conditions found on the device (instance capacity
  *    exceeded, non-finite projected values) are recorded in an error word inside
  *    `proj` and reported by ges_sync_status.
- *  - Arrays are float32, row-major, C-contiguous. All views of a call are
+ *  - Arrays are float32 (the colour input may instead be 16-bit, see
+ *    ges_config.color_storage), row-major, C-contiguous. All views of a call are
  *    concatenated: pixel arrays hold view 0's pixels, then view 1's, etc.
  *  - The calls are not thread-safe for one `proj` / `bins` pair; distinct
  *    buffers may be used concurrently on distinct streams.
  *
- * Readings where the paper is silent (the full list with reasons is in the
- * repository's design notes):
+ * Readings where the paper is silent:
  *  - phi_mode 1 (default): phi(beta) = 2 / (1 + exp(-rho (beta - 2))), so
  *    phi(2) = 1 and beta = 2 is the 3DGS Gaussian; phi_mode 2 evaluates Eq. 7
  *    as printed, 2 / (1 + exp(-(rho beta - 2 beta))); phi_mode 0 is phi = 1.
