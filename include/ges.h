@@ -179,7 +179,8 @@ GES_API ges_status ges_bin(int32_t n, int32_t n_views, const ges_camera *cams, c
  *   n_contrib [P] number of blended splats
  *   n_eval  [P]  number of tile-list entries the pixel evaluated before it ended
  *                (the work count of the pixel; used for roofline accounting)
- * normal and n_eval may be NULL (not written). */
+ * depth, normal and n_eval may be NULL (not written); with neither depth nor normal (a
+ * render for a loss on the colour, as in training) their accumulations are left out. */
 GES_API ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
                                   const void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes,
                                   float *color, float *depth, float *alpha, float *normal, float *t_final,

@@ -421,10 +421,14 @@ class Rasterizer:
                 self._alloc_bins(max(1024, int(math.ceil(m * self.headroom))))
         ges_bin(self.n, self.n_views, self.cams_c, self.cfg_c, self.proj, self.bins, stream)
 
-    def render_fwd(self, stream=None, n_eval: Optional[torch.Tensor] = None) -> Dict[str, torch.Tensor]:
+    def render_fwd(self, stream=None, n_eval: Optional[torch.Tensor] = None,
+                   depth_normal: bool = True) -> Dict[str, torch.Tensor]:
+        """S6. depth_normal=False leaves the depth and normal outputs unwritten (and their
+        accumulation out), for renders that only feed a loss on the colour."""
         o = self.out
-        ges_render_fwd(self.n, self.n_views, self.cams_c, self.cfg_c, self.proj, self.bins, o["color"], o["depth"],
-                       o["alpha"], o["normal"], o["t_final"], o["last"], o["n_contrib"], n_eval, stream)
+        ges_render_fwd(self.n, self.n_views, self.cams_c, self.cfg_c, self.proj, self.bins, o["color"],
+                       o["depth"] if depth_normal else None, o["alpha"], o["normal"] if depth_normal else None,
+                       o["t_final"], o["last"], o["n_contrib"], n_eval, stream)
         return o
 
     def forward(self, pos_op, lscale_beta, quat, color, stream=None) -> Dict[str, torch.Tensor]:

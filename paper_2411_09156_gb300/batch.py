@@ -78,7 +78,8 @@ class BatchPlan:
             r.preprocess(*x)
             r.bin()
         elif name == "render_fwd":
-            r.render_fwd()
+            # a training step's loss reads the colour only: depth and normal are not rendered
+            r.render_fwd(depth_normal=self.target is None)
         elif name == "loss":
             ges_loss_rgb(r.n_views, r.cams_c, r.out["color"], self.target, self.lam, self.loss_ws, self.loss,
                          self.g_color_loss)

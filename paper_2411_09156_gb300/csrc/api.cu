@@ -270,8 +270,7 @@ ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *cams, co
                           const void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes, float *color,
                           float *depth, float *alpha, float *normal, float *t_final, uint32_t *last,
                           uint32_t *n_contrib, uint32_t *n_eval, void *stream) {
-    if (!check_views(n, n_views, cams, cfg) || !proj || !bins || !color || !depth || !alpha || !t_final || !last ||
-        !n_contrib)
+    if (!check_views(n, n_views, cams, cfg) || !proj || !bins || !color || !alpha || !t_final || !last || !n_contrib)
         return GES_ERR_INVALID_ARG;
     const ProjLayout PL = proj_layout(n, n_views);
     if (proj_bytes < PL.bytes) return GES_ERR_INVALID_ARG;

@@ -106,7 +106,9 @@ __device__ __forceinline__ bool load_cull_stage(const float4 *rec, uint32_t e, f
     return true;
 }
 
-template <int TW, int TH>
+// DN: the depth and normal outputs are wanted; without them (the training step renders for a
+// loss on the colour) their accumulations drop out.
+template <int TW, int TH, bool DN>
 __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
     constexpr int NW = TW * TH / 32;
     __shared__ float4 s_rec[NW][32][4];  // per-warp slot of the current chunk's records
@@ -159,10 +161,12 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
                 C0 = __fmaf_rn(w, r2.x, C0);
                 C1 = __fmaf_rn(w, r2.y, C1);
                 C2 = __fmaf_rn(w, r2.z, C2);
-                D = __fmaf_rn(w, r2.w, D);
-                N0 = __fmaf_rn(w, r3.x, N0);
-                N1 = __fmaf_rn(w, r3.y, N1);
-                N2 = __fmaf_rn(w, r3.z, N2);
+                if (DN) {
+                    D = __fmaf_rn(w, r2.w, D);
+                    N0 = __fmaf_rn(w, r3.x, N0);
+                    N1 = __fmaf_rn(w, r3.y, N1);
+                    N2 = __fmaf_rn(w, r3.z, N2);
+                }
                 T = Tn;
                 ++cnt;
                 last = c0 + (uint32_t)bit + 1;
@@ -177,9 +181,9 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
             col[0] = __fmaf_rn(T, a.bg[0], C0);
             col[P] = __fmaf_rn(T, a.bg[1], C1);
             col[2 * P] = __fmaf_rn(T, a.bg[2], C2);
-            a.depth[g] = D;
+            if (DN && a.depth) a.depth[g] = D;
             a.alpha[g] = 1.f - T;
-            if (a.normal) {
+            if (DN && a.normal) {
                 float *nrm = a.normal + 3 * a.V.pix_base[v] + pix;
                 nrm[0] = N0; nrm[P] = N1; nrm[2 * P] = N2;
             }
@@ -374,12 +378,6 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
     }
 }
 
-template <int TW, int TH>
-static cudaError_t launch_fwd_t(const FwdArgs &a, int grid, cudaStream_t s) {
-    k_render_fwd<TW, TH><<<grid, TW * TH, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
 // Persistent grid: as many CTAs of `kernel` as fit on every SM at once.
 template <class K>
 static int persistent_grid(K kernel, int threads) {
@@ -390,6 +388,16 @@ static int persistent_grid(K kernel, int threads) {
     if (per < 1) per = 1;
     return sms * per;
 }
+
+template <int TW, int TH, bool DN>
+static cudaError_t launch_fwd_t(const FwdArgs &a, cudaStream_t s) {
+    int grid = a.V.n_tiles;
+    if (a.queue) grid = min(grid, persistent_grid(k_render_fwd<TW, TH, DN>, TW * TH));
+    if (grid <= 0) return cudaSuccess;
+    k_render_fwd<TW, TH, DN><<<grid, TW * TH, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 
 template <int TW, int TH, bool FULL>
 static cudaError_t launch_bwd_t(const BwdArgs &a, cudaStream_t s) {
@@ -404,20 +412,13 @@ bool tile_shape_supported(int tw, int th) {
     return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8) || (tw == 8 && th == 32);
 }
 
-template <int TW, int TH>
-static cudaError_t launch_fwd_shape(const FwdArgs &a, cudaStream_t s) {
-    int grid = a.V.n_tiles;
-    if (a.queue) grid = min(grid, persistent_grid(k_render_fwd<TW, TH>, TW * TH));
-    if (grid <= 0) return cudaSuccess;
-    return launch_fwd_t<TW, TH>(a, grid, s);
-}
-
 cudaError_t launch_render_fwd(const FwdArgs &a, cudaStream_t s) {
     const int tw = a.V.tile_w, th = a.V.tile_h;
-    if (tw == 16 && th == 16) return launch_fwd_shape<16, 16>(a, s);
-    if (tw == 8 && th == 8) return launch_fwd_shape<8, 8>(a, s);
-    if (tw == 8 && th == 32) return launch_fwd_shape<8, 32>(a, s);
-    return launch_fwd_shape<32, 8>(a, s);
+    const bool dn = a.depth != nullptr || a.normal != nullptr;
+    if (tw == 16 && th == 16) return dn ? launch_fwd_t<16, 16, true>(a, s) : launch_fwd_t<16, 16, false>(a, s);
+    if (tw == 8 && th == 8) return dn ? launch_fwd_t<8, 8, true>(a, s) : launch_fwd_t<8, 8, false>(a, s);
+    if (tw == 8 && th == 32) return dn ? launch_fwd_t<8, 32, true>(a, s) : launch_fwd_t<8, 32, false>(a, s);
+    return dn ? launch_fwd_t<32, 8, true>(a, s) : launch_fwd_t<32, 8, false>(a, s);
 }
 
 cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s) {

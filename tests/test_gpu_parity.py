@@ -227,6 +227,25 @@ def test_tile_shapes_batches_and_persistent_are_bit_identical():
             assert torch.equal(out[k], base[k]), (cfg, k)
 
 
+def test_colour_only_forward_equals_the_full_forward():
+    """Without depth and normal outputs (a render for a loss on the colour) the forward leaves
+    their accumulations out; everything it does write is bit-identical to the full render."""
+    sc = make_scene(4000, 41, "object", 3)
+    cams = [look_at((0.3, -2.4, 0.6), (0, 0, 0), 150, 110), look_at((-1.5, 1.9, 0.8), (0, 0, 0), 97, 131)]
+    for persistent in (0, 1):
+        cfg = api.GESConfig(sh_degree=3, persistent=persistent)
+        rast, _ = H.gpu_forward(sc, cams, cfg)
+        full = {k: rast.out[k].clone() for k in ("color", "alpha", "t_final", "last", "n_contrib")}
+        depth = rast.out["depth"].clone()
+        rast.out["depth"].fill_(-7.0)
+        rast.render_fwd(depth_normal=False)
+        torch.cuda.synchronize()
+        for k, v in full.items():
+            assert torch.equal(rast.out[k], v), k
+        assert (rast.out["depth"] == -7.0).all()  # not written
+        assert not torch.equal(depth, rast.out["depth"])
+
+
 @pytest.mark.parametrize("n_views,sh_degree", [(4, 2), (5, 3), (20, 3)])
 def test_batched_views_equal_per_view_calls(n_views, sh_degree):
     """The batched launch gives each view the image of a one-view call, and the sum of the one-view
