@@ -198,6 +198,12 @@ def test_levelset_single_pixel_and_no_points():
     pixels = np.stack([np.zeros(64 * 48, np.int32), np.arange(64 * 48, dtype=np.int32)], 1)
     got = _run(sc, cams, depth, alpha, np.ascontiguousarray(pixels), 32, 1)
     assert not got.any()
+    # pixels naming a view that does not exist or an index outside the view give no point,
+    # whatever the depth and alpha buffers hold
+    depth, alpha = np.full(64 * 48, 4.0, np.float32), np.ones(64 * 48, np.float32)
+    bad = np.array([[-1, 10], [1, 10], [5, 0], [0, -3], [0, 64 * 48], [0, 1 << 30]], np.int32)
+    got = _run(sc, cams, depth, alpha, bad, 32, 1)
+    assert not got.any()
 
 
 def test_levelset_invalid_arguments():
