@@ -96,3 +96,12 @@ def test_points_host_checks():
     out = torch.empty((5, 16), dtype=torch.int32, device="cuda")
     with pytest.raises(api.GESError):  # points off the 16-byte grid
         api.ges_knn_points(100, pos, 4, pts.view(-1)[1:17], ws, out)
+
+
+def test_single_point_query():
+    pos = make_scene(2000, 13, "uniform", -1).pos_op.astype(np.float64)
+    q = np.array([[0.1, -0.2, 0.3, 1.0]])
+    got = _run(pos.astype(np.float32), q)
+    assert got.shape == (1, 16)
+    _check(pos, q, got, min_sep=0.0)
+

@@ -397,3 +397,22 @@ def test_step_from_host_buffers_equals_the_device_step():
         for k, v in ref.items():
             a, b = host_out[k].double(), v.cpu().double()
             assert float((a - b).norm() / b.norm()) <= 1e-4, k
+
+
+def test_preprocess_ranges_equal_the_whole_call():
+    """S1-S4 over splat ranges (empty ones included) write the records of the single call and the
+    same instance total."""
+    sc = make_scene(3001, 81, "object", 3)
+    cams = [look_at((0.4, -2.3, 0.8), (0, 0, 0), 120, 90), look_at((-1.8, 1.1, 0.6), (0, 0, 0), 64, 80)]
+    cfg = api.GESConfig(sh_degree=3)
+    t = api.scene_tensors(sc)
+    whole = api.Rasterizer(sc.n, cams, cfg)
+    whole.preprocess(*t)
+    parts = api.Rasterizer(sc.n, cams, cfg)
+    for first, count in ((0, 1000), (1000, 0), (1000, 1), (1001, 2000), (3001, 0)):
+        parts.preprocess_range(first, count, *t)
+    torch.cuda.synchronize()
+    assert parts.instance_count() == whole.instance_count()
+    a, b = whole.proj_views(), parts.proj_views()
+    assert torch.equal(a["rec"], b["rec"]) and torch.equal(a["binrec"], b["binrec"])
+
