@@ -41,6 +41,9 @@ def _check(pos, q, got, min_sep=0.9):
     tol = 1e-6 * np.maximum(dr[:, 15:16], 1e-6) + 1e-6 * (np.abs(qv).max(1, keepdims=True) + 1.0)
     assert (np.diff(dg, axis=1) >= -tol).all(), "lists not ordered"
     assert (dg[:, 15] <= dr[:, 15] + tol[:, 0]).all(), "a listed neighbour is farther than the 16th nearest"
+    if ref.shape[1] < 17:  # sixteen centres in all: every list is all of them
+        assert all(set(a) == set(b) for a, b in zip(g, ref))
+        return
     sep = dr[:, 16] - dr[:, 15] > 10 * tol[:, 0]
     same = np.array([set(a) == set(b[:16]) for a, b in zip(g, ref)])
     assert same[sep].all()
@@ -104,4 +107,16 @@ def test_single_point_query():
     got = _run(pos.astype(np.float32), q)
     assert got.shape == (1, 16)
     _check(pos, q, got, min_sep=0.0)
+
+
+def test_smallest_cloud_of_sixteen_centres():
+    """n = 16, the smallest size: every list holds all sixteen centres, ordered by distance."""
+    rng = np.random.default_rng(17)
+    pos = np.concatenate([rng.uniform(-1, 1, (16, 3)), np.ones((16, 1))], 1)
+    q = np.concatenate([rng.uniform(-2, 2, (40, 3)), np.ones((40, 1))], 1)
+    got = _run(pos.astype(np.float32), q)
+    assert all(set(r) == set(range(16)) for r in got)
+    _check(pos, q, got, min_sep=0.0)
+    lists = api.knn(torch.from_numpy(pos.astype(np.float32)).cuda()).cpu().numpy()
+    assert all(set(r) == set(range(16)) for r in lists) and (lists[:, 0] == np.arange(16)).all()
 
