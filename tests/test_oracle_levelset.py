@@ -115,3 +115,43 @@ def test_first_crossing_from_the_camera_side():
     assert -0.2 - 4 * s < z < -0.2, z  # on the camera side of the near splat
     d = OLS.density_at(pos, lsb, q, out["neighbours"], out["point"], phi_mode=0)
     assert abs(d - 0.3) < 1e-3
+
+
+def _axis_splat(ls_flat):
+    # a flat beta = 2 splat facing a 65x65 camera whose centre pixel (32, 32) looks straight down
+    # the optical axis: along that ray the splat's spread is its flat scale exactly
+    pos, lsb, q = _scene([0.0, 0.0, 0.0], [np.log(0.5), np.log(0.5), ls_flat], [1.0, 0, 0, 0], o=0.9)
+    return pos, lsb, q, _cam(w=65, h=65)
+
+
+def test_march_samples_the_printed_range_of_sigma():
+    # Sec. 3.3: t_k runs over [-3 sigma_g(v), 3 sigma_g(v)] (k = 3 from the golden fixture);
+    # sigma_g(v) here is the flat scale s in closed form (v is the splat's flat axis)
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+    k = gold["march_half_width_sigmas"]["value"]
+    s = 0.02
+    pos, lsb, q, cam = _axis_splat(np.log(s))
+    for n_steps in (2, 7, 32):
+        out = OLS.extract(pos, lsb, q, cam, depth=4.0, alpha=1.0, px=32, py=32, n_steps=n_steps, phi_mode=0)
+        ts = out["ts"]
+        assert len(ts) == n_steps
+        np.testing.assert_allclose([ts[0], ts[-1]], [-k * s, k * s], rtol=1e-12)
+        np.testing.assert_allclose(np.diff(ts), 2 * k * s / (n_steps - 1), rtol=1e-9)
+
+
+def test_crossing_between_two_and_three_sigma_is_found_and_beyond_three_is_not():
+    # start x0 on the camera side of the splat at world z = -c s (camera depth 4 - c s). Along the
+    # axis d(z) = 0.9 exp(-(z / s)^2 / 2) first reaches the level 0.3 at z = -s sqrt(2 ln 3), so
+    # the crossing lies at t = (c - sqrt(2 ln 3)) s from x0: 2.52 s for c = 4 (inside +-3 sigma,
+    # outside +-2 sigma) and 3.22 s for c = 4.7 (outside +-3 sigma, inside +-4 sigma)
+    s = 0.02
+    zc = np.sqrt(2.0 * np.log(0.9 / 0.3))
+    pos, lsb, q, cam = _axis_splat(np.log(s))
+    out = OLS.extract(pos, lsb, q, cam, depth=4.0 - 4.0 * s, alpha=1.0, px=32, py=32, n_steps=601, phi_mode=0)
+    assert out["valid"] and not out["flag"]
+    assert abs(out["t"] - (4.0 - zc) * s) < 1e-3 * s
+    np.testing.assert_allclose(out["point"], [0.0, 0.0, -zc * s], atol=1e-3 * s)
+    out = OLS.extract(pos, lsb, q, cam, depth=4.0 - 4.7 * s, alpha=1.0, px=32, py=32, n_steps=601, phi_mode=0)
+    assert not out["valid"] and out["hit"] == -1
