@@ -176,3 +176,43 @@ def test_far_sample_with_underflowing_density_keeps_a_defined_normal():
     u = A @ x / np.linalg.norm(A @ x)
     nrm = R[:, 2] * np.sign(R[:, 2] @ x)
     np.testing.assert_allclose(out["cos"][0], u @ nrm, rtol=0, atol=1e-12)
+
+
+def test_losses_are_the_means_of_eq12_and_eq13_over_samples():
+    # Eq. 12 and Eq. 13 average over the sample points. Two isolated axis-aligned splats (phi off,
+    # identity rotations, smallest scale on z), each listed with 15 far splats of zero opacity, and
+    # three samples x = mu + s * z. For one splat of opacity o and shape beta: Q = |z|^2, d =
+    # o exp(-Q^(beta/2) / 2), so f = s_z sqrt(Q^(beta/2) - 2 ln o); e = s_z |z_3| gives
+    # fbar = s_z |z_3|^(beta/2); -grad d is along Sigma^-1 (x - mu) = z / s, and n* = (0, 0, sign z_3).
+    n = 17
+    pos = np.zeros((n, 4))
+    pos[1, :3] = [5.0, 0.0, 0.0]
+    pos[2:, :3] = 100.0 + 3.0 * np.arange(15)[:, None]
+    pos[0, 3], pos[1, 3] = 0.8, 0.6
+    lsb = np.zeros((n, 4))
+    lsb[:, :3] = np.log([0.3, 0.2, 0.05])
+    lsb[0, 3], lsb[1, 3], lsb[2:, 3] = 2.0, 4.0, 2.0
+    q = np.tile([1.0, 0, 0, 0], (n, 1))
+    knn = np.zeros((n, 16), np.int64)
+    knn[:, 1:] = np.arange(2, 17)
+    knn[1, 0] = 1
+    js = np.array([0, 0, 1])
+    z = np.array([[0.4, -0.3, 0.5], [-0.2, 0.1, -0.25], [0.3, 0.2, 0.6]])
+    s = np.array([0.3, 0.2, 0.05])
+    o, beta = pos[js, 3], lsb[js, 3]
+    Q = (z ** 2).sum(1)
+    f = s[2] * np.sqrt(Q ** (beta / 2) - 2 * np.log(o))
+    fbar = s[2] * np.abs(z[:, 2]) ** (beta / 2)
+    u = (z / s) / np.linalg.norm(z / s, axis=1, keepdims=True)
+    nstar = np.zeros((3, 3))
+    nstar[:, 2] = np.sign(z[:, 2])
+    want_sdf = np.mean(np.abs(fbar - f))
+    want_nor = np.mean(((u - nstar) ** 2).sum(1))
+    out = OG.evaluate(pos, lsb, q, knn, js, z, phi_mode=0, lambda_sdf=1.0, lambda_nor=0.5, with_grad=False)
+    np.testing.assert_allclose(out["f"], f, rtol=1e-12)
+    np.testing.assert_allclose(out["fbar"], fbar, rtol=1e-12)
+    np.testing.assert_allclose(out["cos"], (u * nstar).sum(1), rtol=1e-12)
+    np.testing.assert_allclose(out["l_sdf"], want_sdf, rtol=1e-12)
+    np.testing.assert_allclose(out["l_nor"], want_nor, rtol=1e-12)
+    np.testing.assert_allclose(out["loss"], want_sdf + 0.5 * want_nor, rtol=1e-12)
+    assert not out["flags"].any()
