@@ -112,6 +112,13 @@ def oracle_upstream(rast, grads, v, pixels=None):
     return c, d, a, n
 
 
+# Per-tensor gradient errors of every compare_grads call in this run, printed by
+# tests/conftest.py at the end of the session: the tensor-level relative L2, and the largest
+# elementwise error in the form |d| / max(|g|, 1e-2 rms(g)) (bound 1e-3 in the method's
+# parity contract) with the number of elements above 1e-3 in that form.
+GRAD_REPORT = []
+
+
 def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=3e-3, floor=0.25, rows=None):
     """Tensor-level relative L2 <= 1e-3 (the gradient tolerance) and, as a guard against a wrong
     formula for a single parameter, elementwise |d| <= elem * max(|g|, floor * rms(g)).
@@ -120,8 +127,11 @@ def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=3e-3, floor=0.2
     replay: the colour/depth/normal behind a splat is the final value minus the
     prefix sum, so a splat deep in a pixel's list (T_i ~ 1e-4) carries an absolute
     error of a few ulp of the final value, i.e. a relative error up to ~1e-3 of its
-    own small gradient."""
+    own small gradient. Each call also records the error in the tighter form
+    |d| / max(|g|, 1e-2 rms(g)) in GRAD_REPORT."""
+    import os
     rep = {}
+    test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
     for k in ("g_pos_op", "g_lscale_beta", "g_quat", "g_color"):
         a = np.asarray(got[k], np.float64).reshape(len(got[k]), -1)
         b = np.asarray(ref[k], np.float64).reshape(len(ref[k]), -1)
@@ -130,8 +140,14 @@ def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=3e-3, floor=0.2
         den = np.linalg.norm(b)
         r = float(np.linalg.norm(a - b) / max(den, 1e-30))
         rms = float(np.sqrt(np.mean(b * b))) if b.size else 0.0
-        bad = np.abs(a - b) > elem * np.maximum(np.abs(b), floor * rms)
-        rep[k] = dict(rel_l2=r, max_abs=float(np.abs(a - b).max()) if a.size else 0.0, n_bad=int(bad.sum()))
+        d = np.abs(a - b)
+        bad = d > elem * np.maximum(np.abs(b), floor * rms)
+        tight = d / np.maximum(np.maximum(np.abs(b), 1e-2 * rms), 1e-30)
+        rep[k] = dict(rel_l2=r, max_abs=float(d.max()) if a.size else 0.0, n_bad=int(bad.sum()),
+                      tight_max=float(tight.max()) if a.size else 0.0, tight_over=int((tight > 1e-3).sum()),
+                      guard_max=float((d / np.maximum(np.maximum(np.abs(b), floor * rms), 1e-30)).max())
+                      if a.size else 0.0, n=int(a.size))
+        GRAD_REPORT.append(dict(test=test, tensor=k, **rep[k]))
         assert r <= rel_l2, (k, rep[k])
         assert bad.sum() == 0, (k, rep[k])
     return rep
