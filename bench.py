@@ -10,6 +10,15 @@ preprocess backward, run as captured CUDA graphs (persistent render over a
 longest-first tile queue). The same views are also timed through the plain
 one-view-per-launch path for comparison ("per_view").
 
+Beside the headline: per-kernel rooflines of the render kernels against FP32-FMA and
+ex2 peaks measured on the GPU by the library's microbenchmarks ("rooflines",
+"peaks_measured"), HBM fractions of preprocess, binning and preprocess backward
+("hbm_stages"), the end-to-end step from pinned host buffers with the host link's
+own bandwidth ("e2e"), the training step with the Eq. 8 loss, binary16 colour
+storage, the GSR and level-set legs, and the other workloads ("other_workloads":
+the 1k-splat, 100k-splat and 1.5M-splat single views, and the 3M-splat 16-view
+batch against 16 sequential one-view steps).
+
 Prints one JSON line (rank 0). With --impl reference it times the FP64 CPU
 oracle instead (the reference arm of this benchmark), on a bounded pixel sample.
 Under torchrun each rank renders its own independent batch of views (weak
@@ -38,6 +47,8 @@ METRIC = "fwd+bwd Mpixel/s at 1.5M splats, batched vs per-view, and % of HBM roo
 F_TEST = 10          # FP32 flops per evaluated (pixel, list entry) pair: dx, dy, Q
 F_BLEND_FWD = 26     # per blended pair in the forward (falloff, alpha, transmittance, 7 accumulations)
 F_BLEND_BWD = 104    # per blended pair in the backward replay (forward blend + 78 gradient flops)
+MUFU_FWD = 3         # special-function operations per blended pair: log2 Q, exp2 for Q^(beta/2), exp2 for G
+MUFU_BWD = 6         # the replay's three, rcp(1 - alpha), rcp(Q) and log2 Q of the beta gradient
 F_LOSS = 1188        # per pixel of the Eq. 8 loss and its gradient (3 channels x 396: 5 window maps x 2
                      # separable passes x 11 taps x 2, 3 derivative maps likewise, products, SSIM terms)
 
@@ -58,6 +69,8 @@ def parse_args():
     p.add_argument("--no-train-step", action="store_true", help="skip the step with the Eq. 8 loss")
     p.add_argument("--no-color16", action="store_true", help="skip the step with binary16 colour storage")
     p.add_argument("--no-gsr", action="store_true", help="skip the KNN build, the GSR point evaluation and the level-set extraction")
+    p.add_argument("--no-other-workloads", action="store_true",
+                   help="skip the other workloads (tiny, object, one-view scene, 3M-splat 16-view batch)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the oracle sample")
     p.add_argument("--splats", type=int, default=None,
                    help="override the workload's splat count (smaller cases for profiling; not a bench line)")
@@ -195,6 +208,119 @@ def timed_call(fn, warmup: int, steps: int, flush, world: int) -> float:
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     return max_over_ranks(statistics.mean(ts), world)
+
+
+def render_roofline(kname: str, t_ms: float, blended: int, f_blend: int, mufu_blend: int, dense_flops: int,
+                    events: int, pk: dict) -> dict:
+    """Roofline of a render kernel against the measured FP32-FMA and ex2 peaks of this GPU.
+    achieved: the method's arithmetic, f_blend FP32 flops per blended pair (the pairs the
+    compositing needs); beside it the dense equivalent that also charges every (pixel, list entry)
+    pair walked a support test, and the (pixel, splat) lane pairs the warps actually evaluate
+    (32 per pair of an 8x4 block and a splat that passed the warp cull)."""
+    t = t_ms / 1e3
+    fl = f_blend * blended
+    traffic, _ = profile_traffic(kname)
+    mu = mufu_blend * blended
+    return {"bound": "alu", "kernel": kname, "achieved": fl / t / 1e12, "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+            "frac": fl / t / 1e12 / pk["fp32_tflops"], "traffic": traffic,
+            "peak_source": f"measured: FP32 FMA microbenchmark (ges_peak_run) on this GPU, {pk['sm_count']} SMs",
+            "flops_per_launch": fl, "flops_per_blended_pair": f_blend, "time_ms": t_ms,
+            "dense_equivalent": {"flops_per_launch": dense_flops + fl,
+                                 "frac": (dense_flops + fl) / t / 1e12 / pk["fp32_tflops"]},
+            "lane_pairs_evaluated": 32 * events,
+            "mufu": {"ops_per_launch": mu, "achieved_gops": mu / t / 1e9, "peak_gops": pk["mufu_ex2_gops"],
+                     "frac": mu / t / 1e9 / pk["mufu_ex2_gops"], "ops_per_blended_pair": mufu_blend}}
+
+
+def hbm_stage_fractions(plan, sc, cams, n_inst: int, flush, hbm: float, warmup: int, steps: int, world: int) -> dict:
+    """Preprocess (K1), binning (K2-K5) and preprocess backward (K8) timed alone (eager calls,
+    L2 flushed) against the measured HBM copy bandwidth, with the algorithmic bytes per unit of
+    the method: K1 reads each splat's attributes once (48 B + the colour) and writes a 64 B render
+    and a 32 B binning record per (splat, view); binning moves 28 B per (splat, view) and 44 B per
+    instance; K8 reads the 64 B screen gradient per (splat, view) and each splat's attributes and
+    writes its gradients once."""
+    r, x = plan.rast, plan.inputs
+    n, nv = sc.n, sc.n * len(cams)
+    col = x[3].numel() * x[3].element_size() // max(n, 1)
+    b_k1 = n * (48 + col) + nv * 96
+    b_bin = 28 * nv + 44 * n_inst
+    b_k8 = nv * 64 + n * (48 + col) + n * (48 + 4 * (col // x[3].element_size()))
+    t_k1 = timed_call(lambda: r.preprocess(*x), warmup, steps, flush, world)
+    t_bin = timed_call(lambda: r.bin(), warmup, steps, flush, world)
+    t_k8 = timed_call(lambda: r.preprocess_bwd(*x, plan.grads), warmup, steps, flush, world)
+    out = {}
+    for k, b, t in (("k_preprocess", b_k1, t_k1), ("binning", b_bin, t_bin), ("k_preprocess_bwd", b_k8, t_k8)):
+        gbs = b / (t / 1e3) / 1e9
+        out[k] = {"bytes": b, "time_ms": t, "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm}
+    return out
+
+
+def host_link_gbs(nbytes: int = 1 << 29) -> dict:
+    """Pinned host <-> device bandwidth of one large cudaMemcpyAsync per direction (best of 5)."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    res = {}
+    for name, fn in (("h2d", lambda: d.copy_(h, non_blocking=True)), ("d2h", lambda: h.copy_(d, non_blocking=True))):
+        best = 0.0
+        fn()
+        torch.cuda.synchronize()
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = max(best, nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        res[name] = best
+    return res
+
+
+def other_workloads(cfg, args, flush, rank: int, world: int) -> dict:
+    """fwd+bwd Mpixel/s of the other workloads with the main line's tile shape and prefetch
+    distance, timed like the main line (graphed steps, L2 flushed, random upstream gradients):
+    the 1k-splat 128x128 view, the 100k-splat 800x800 view, the 1.5M-splat 1600x1040 view, and the
+    3M-splat 16-view batch both batched and as 16 sequential one-view steps."""
+    import torch
+    from paper_2411_09156_gb300 import api
+    from paper_2411_09156_gb300.batch import BatchPlan
+    out = {}
+    for name in ("tiny-1k-128", "object-100k-800", "scene-1.5M-1600x1040", "drt16-3M"):
+        sc, cams = make_workload(name, rank)
+        inputs = api.scene_tensors(sc)
+        P = sum(c.width * c.height for c in cams)
+        ups = upstream_grads(P, 4000 + rank)
+        c = dataclasses.replace(cfg, sh_degree=sc.sh_degree)
+        plan = BatchPlan(sc.n, cams, c, inputs, ups)
+        ms = timed_call(plan.step, args.warmup, args.steps, flush, world)
+        plan.check()
+        rec = {"value": world * P / (ms / 1e3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ms, "splats": sc.n,
+               "views": len(cams), "pixels": P, "gpu_launches": plan.launches_per_step() * args.steps}
+        del plan
+        if len(cams) > 1:
+            pv_cfg = c.replace(persistent=0)
+            plans, base = [], 0
+            for cam in cams:
+                w, h = cam.width, cam.height
+                u = [ups[0][3 * base:3 * base + 3 * w * h], ups[1][base:base + w * h], ups[2][base:base + w * h],
+                     ups[3][3 * base:3 * base + 3 * w * h]]
+                plans.append(BatchPlan(sc.n, [cam], pv_cfg, inputs, u))
+                base += w * h
+
+            def seq():
+                for p_ in plans:
+                    p_.step()
+
+            pv = timed_call(seq, args.warmup, args.steps, flush, world)
+            for p_ in plans:
+                p_.check()
+            rec["per_view"] = {"value": world * P / (pv / 1e3) / 1e6, "unit": "Mpixel/s", "ms_per_step": pv,
+                               "launches": f"{len(cams)} sequential one-view steps, each as CUDA graphs"}
+            del plans
+        out[name] = rec
+        del inputs, ups
+        torch.cuda.empty_cache()
+    return out
 
 
 def levelset_launches(n: int) -> int:
@@ -343,9 +469,12 @@ def main():
         tiles = lay.tile_base[v] + (ys // th) * ((w + tw - 1) // tw) + xs // tw
         starts[plan.rast.pix_base[v]:plan.rast.pix_base[v + 1]] = ranges[tiles.reshape(-1), 0].long()
     evals_bwd = int((o["last"].long() - starts).double().sum().item())
+    events = plan.rast.cull_events()
     n_inst = plan.rast.instance_count()
     plan.step()  # restore the step's own state
     torch.cuda.synchronize()
+    from paper_2411_09156_gb300 import peaks as PK
+    pk = PK.measure()
 
     # timed region
     sampler = ClockSampler(local)
@@ -370,30 +499,27 @@ def main():
     st = plan.rast.sync_status()
     if st != 0:
         raise RuntimeError(f"device status {st} after the timed steps")
+    launches_main = plan.launches_per_step() * args.steps
     stage_avg = [statistics.mean(s[i] for s in stage_ms) for i in range(4)]
     names = ["preprocess_bin", "render_fwd", "render_bwd", "preprocess_bwd"]
 
     # roofline of the dominant kernel
     dom = int(np.argmax(stage_avg))
-    sm_mhz = clocks.get("sm_mhz") or 1447.0
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled SM clock
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    flops_fwd = F_TEST * evals_fwd + F_BLEND_FWD * blended
-    flops_bwd = F_TEST * evals_bwd + F_BLEND_BWD * blended
-    kernels = {"render_fwd": ("k_render_fwd", flops_fwd), "render_bwd": ("k_render_bwd", flops_bwd)}
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
+    fp32_peak = pk["fp32_tflops"]
+    kernels = {"render_fwd": ("k_render_fwd", F_BLEND_FWD, MUFU_FWD, F_TEST * evals_fwd),
+               "render_bwd": ("k_render_bwd", F_BLEND_BWD, MUFU_BWD, F_TEST * evals_bwd)}
+    rooflines = {k: render_roofline(kn, stage_avg[names.index(k)], blended, fb, mb, dense, events, pk)
+                 for k, (kn, fb, mb, dense) in kernels.items()}
     if names[dom] in kernels:
-        kname, fl = kernels[names[dom]]
-        achieved = fl / (stage_avg[dom] / 1e3) / 1e12
-        traffic, _ = profile_traffic(kname)
-        roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp32_peak, "traffic": traffic,
-                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled median)",
-                    "flops_per_launch": fl}
+        roofline = rooflines[names[dom]]
     else:
         roofline = {"bound": "hbm", "kernel": names[dom], "achieved": None, "peak": hbm, "unit": "GB/s",
                     "frac": None, "traffic": None}
+    hbm_stages = hbm_stage_fractions(plan, sc, cams, n_inst, flush, hbm, args.warmup, args.steps, world)
 
     # per-view path (one launch sequence per view, each captured as graphs)
     per_view = None
@@ -454,7 +580,10 @@ def main():
             e_ms.append(e0.elapsed_time(e1))
         em = max_over_ranks(statistics.mean(e_ms), world)
         e2e = {"value": world * P / (em / 1e3) / 1e6, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": em}
+               "d2h_bytes_per_step": d2h, "ms_per_step": em, "host_link_gbs": host_link_gbs(),
+               "copy_bound_ms": None}
+        lk = e2e["host_link_gbs"]
+        e2e["copy_bound_ms"] = 1e3 * (h2d / (lk["h2d"] * 1e9) + d2h / (lk["d2h"] * 1e9))
 
     # precision variant: the colour input (SH coefficients) stored as IEEE binary16 and widened
     # to float32 on load; the same batched step otherwise
@@ -580,6 +709,12 @@ def main():
         del lws, pts, pix
         torch.cuda.empty_cache()
 
+    others = None
+    if not args.no_other_workloads and args.splats is None:
+        del plan
+        torch.cuda.empty_cache()
+        others = other_workloads(cfg, args, flush, rank, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, npx, secs, cores = cpu_baseline(sc, cams, cfg, args.cpu_seconds)
@@ -600,16 +735,21 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single-gpu"},
             "stages_ms": dict(zip(names, stage_avg)),
             "roofline": roofline,
+            "rooflines": rooflines,
+            "hbm_stages": hbm_stages,
+            "peaks_measured": pk,
             "per_view": per_view,
             "e2e": e2e,
             "train_step": train,
             "color_binary16": color16,
             "gsr": gsr,
             "levelset": levelset,
+            "other_workloads": others,
             "cpu_baseline": cpu,
             "clocks": clocks,
-            "gpu_launches": plan.launches_per_step() * args.steps,
-            "work": {"evaluated_pairs_fwd": evals_fwd, "evaluated_pairs_bwd": evals_bwd, "blended_pairs": blended},
+            "gpu_launches": launches_main,
+            "work": {"evaluated_pairs_fwd": evals_fwd, "evaluated_pairs_bwd": evals_bwd, "blended_pairs": blended,
+                     "warp_cull_passes_fwd": events, "lane_pairs_evaluated_fwd": 32 * events},
             "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)

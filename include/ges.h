@@ -178,7 +178,10 @@ GES_API ges_status ges_bin(int32_t n, int32_t n_views, const ges_camera *cams, c
  *                (the tile's start if none): the backward replays [start, last)
  *   n_contrib [P] number of blended splats
  *   n_eval  [P]  number of tile-list entries the pixel evaluated before it ended
- *                (the work count of the pixel; used for roofline accounting)
+ *                (the work count of the pixel; used for roofline accounting). When
+ *                n_eval is given, the call also stores at byte 16 of `bins` (uint64)
+ *                the number of (8x4 pixel block, splat) pairs that passed the warp's
+ *                support cull, i.e. the pairs its warps evaluated 32 pixels at a time
  * depth, normal and n_eval may be NULL (not written); with neither depth nor normal (a
  * render for a loss on the colour, as in training) their accumulations are left out. */
 GES_API ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
@@ -258,7 +261,10 @@ GES_API ges_status ges_preprocess_bwd_range(int32_t n, int32_t first, int32_t co
  * that every GPU which loads the library keeps until the process exits); larger
  * problems return GES_ERR_TOO_LARGE and launch nothing.
  * Set-up: the first call on a device (with that device current) looks up the
- * array's device address; make that first call before any stream capture.
+ * array's device address; make that first call before any stream capture. The
+ * address is kept for the life of the process: after cudaDeviceReset the
+ * library's device code is loaded again, possibly elsewhere, so a process that
+ * resets a device must not call this entry point on it again.
  * Sharing: all calls use the same array, which keeps the previous call's
  * contents; each call zeroes the part it uses on `stream` before accumulating.
  * Calls that overlap on the GPU (different streams, or different threads on the
@@ -420,6 +426,25 @@ GES_API ges_status ges_sync_status(void *proj, size_t proj_bytes, void *stream);
 
 /* Static description of a status code. */
 GES_API const char *ges_status_string(ges_status s);
+
+/* ---------------------------------------------------------------- measurement
+ * Throughput microbenchmarks for the roofline denominators of the issue-bound
+ * kernels (a measurement utility; the paper has no counterpart). One kernel is
+ * launched on `stream`, blocks_per_sm (1..64) CTAs of 256 threads per SM:
+ *   kind 0  FP32 fused multiply-add, 8 independent chains per thread;
+ *           *ops = flops (an FMA counts two)
+ *   kind 1  ex2.approx (special-function unit), 8 chains per thread; *ops = ex2
+ *   kind 2  rcp.approx (special-function unit), 8 chains per thread; *ops = rcp
+ *   kind 3  FP32 atomic adds: each warp adds into `iters` 64-byte lines of
+ *           `sink` chosen by a hash, 16 lanes per line and instruction (the
+ *           render backward's accumulator update); *ops = atomic adds
+ * iters: loop trips per thread (kinds 0-2, 16 operations per chain and trip)
+ * or per warp (kind 3). sink: device buffer of sink_floats floats
+ * (>= 256; for kind 3 a multiple of 16, its lines are the targets and are
+ * modified). *ops (host) receives the operations the launch performs; time the
+ * launch with events on `stream`. */
+GES_API ges_status ges_peak_run(int32_t kind, int32_t blocks_per_sm, int32_t iters, float *sink,
+                                uint64_t sink_floats, void *stream, uint64_t *ops);
 
 /* GES_ABI_VERSION of the loaded library. */
 GES_API int32_t ges_abi_version(void);

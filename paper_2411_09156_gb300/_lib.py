@@ -85,6 +85,7 @@ SIGNATURES = {
                                     _P]),
     "ges_gsr": (ctypes.c_int, [_I, _P, _P, _P, _CFG, _P, _I, _P, _P, ctypes.c_float, ctypes.c_float, _P, _S, _P,
                                _P, _P, _P, _P, _P]),
+    "ges_peak_run": (ctypes.c_int, [_I, _I, _I, _P, ctypes.c_uint64, _P, ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 _lock = threading.Lock()

@@ -475,6 +475,12 @@ class Rasterizer:
     def sync_status(self, stream=None) -> int:
         return ges_sync_status(self.proj, stream)
 
+    def cull_events(self) -> int:
+        """(8x4 pixel block, splat) pairs that passed the forward's warp cull in the last
+        render_fwd call given n_eval (read from the bins header; synchronises)."""
+        torch.cuda.synchronize()
+        return int(self.bins[16:24].view(torch.int64).item())
+
     def instance_count(self, stream=None) -> int:
         """Tile instances produced by the last preprocess (synchronises the stream)."""
         return ges_instance_count(self.proj, stream)

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libges.so")
-SOURCES = ["api.cu", "preprocess.cu", "binning.cu", "render.cu", "noalloc.cu", "loss.cu", "knn.cu", "gsr.cu", "levelset.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "binning.cu", "render.cu", "noalloc.cu", "loss.cu", "knn.cu", "gsr.cu", "levelset.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -288,11 +288,13 @@ ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *cams, co
     a.counter = const_cast<uint32_t *>(at<uint32_t>(bins, 4));
     a.color = color; a.depth = depth; a.alpha = alpha; a.normal = normal; a.t_final = t_final;
     a.last = last; a.n_contrib = n_contrib; a.n_eval = n_eval;
+    a.n_events = n_eval ? const_cast<unsigned long long *>(at<unsigned long long>(bins, 16)) : nullptr;
     a.batch = cfg->batch;
     a.alpha_min = cfg->alpha_min; a.alpha_max = cfg->alpha_max; a.t_min = cfg->t_min;
     for (int c = 0; c < 3; ++c) a.bg[c] = cfg->bg[c];
     a.V = V;
     if (a.queue && cudaMemsetAsync(a.counter, 0, 4, s) != cudaSuccess) return GES_ERR_CUDA;
+    if (a.n_events && cudaMemsetAsync(a.n_events, 0, 8, s) != cudaSuccess) return GES_ERR_CUDA;
     return cuda_status(launch_render_fwd(a, s));
 }
 

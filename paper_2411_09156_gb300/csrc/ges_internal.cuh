@@ -99,7 +99,8 @@ inline uint32_t ceil_div_u64(uint64_t a, uint64_t b) { return (uint32_t)((a + b 
 
 // bins: [header 256][dkey 2 x nV][dval 2 x nV][rank counts nV][rank info nV x 16][ikey 2 x cap]
 //       [ival 2 x cap][ranges T x 8][queue T][hist 256 x nblk][partials]
-// header: u32 n_inst (instances actually listed) at 0, u32 queue counters at 4 and 8.
+// header: u32 n_inst (instances actually listed) at 0, u32 queue counters at 4 and 8, u64 count of
+// the forward's warp-cull passes at 16 (written only when the forward is asked for n_eval).
 struct BinsLayout {
     uint64_t dkey[2], dval[2], rcount, rinfo, ikey[2], ival[2], ranges, queue, hist, partials, bytes;
     uint32_t n_tiles;
@@ -409,6 +410,7 @@ struct FwdArgs {
     uint32_t *counter;
     float *color, *depth, *alpha, *normal, *t_final;
     uint32_t *last, *n_contrib, *n_eval;
+    unsigned long long *n_events;  // with n_eval: (warp block, splat) pairs passing the warp cull
     int batch;
     float alpha_min, alpha_max, t_min;
     float bg[3];

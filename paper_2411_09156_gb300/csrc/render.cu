@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
         const float ry0 = (float)(ty0 + wy0) + 0.5f, ry1 = ry0 + (float)(kWarpH - 1);
         const uint2 rg = a.ranges[tile];
         float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
-        uint32_t cnt = 0, last = rg.x, stop = rg.y;
+        uint32_t cnt = 0, last = rg.x, stop = rg.y, events = 0;
         bool done = !inside;
         uint32_t e_cur = entry_or_none(a.inst_entry, rg.x + lane, rg.y);
         uint32_t e_pf = entry_or_none(a.inst_entry, rg.x + ahead + lane, rg.y);
@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
             const bool hit = load_cull_stage(a.rec, e_cur, rx0, rx1, ry0, ry1, slot, lane);
             e_cur = e_nxt;
             uint32_t mask = __ballot_sync(0xffffffffu, hit);
+            events += __popc(mask);
             __syncwarp();
             while (mask) {
                 const int bit = __ffs(mask) - 1;
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
             a.n_contrib[g] = cnt;
             if (a.n_eval) a.n_eval[g] = stop - rg.x;
         }
+        if (a.n_events && lane == 0) atomicAdd(a.n_events, (unsigned long long)events);
     }
 }
 
