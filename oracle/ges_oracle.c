@@ -35,7 +35,15 @@
  *     kernel's precision, so the order is identical.
  *
  * Per-pixel borderline flags mark decisions that FP32 and FP64 may take
- * differently (support edge, alpha_min edge, t_min edge, normal facing edge).
+ * differently (support edge, alpha_min edge, t_min edge, normal facing edge),
+ * and pixels whose sample point lies within 0.25 px of the centre of a blended
+ * splat with beta < 2, where the falloff of Eq. 3 has a cusp (its mean-position
+ * gradient keeps a finite size but takes its direction from a sub-pixel offset
+ * that float32 screen coordinates do not resolve).
+ *
+ * For large images the per-pixel loop may walk a cell index instead of every
+ * visible splat; that index only leaves out splats whose step of the loop does
+ * nothing (see below), so both give the same result bit for bit.
  */
 #include <math.h>
 #include <stdint.h>
@@ -59,6 +67,8 @@ typedef struct {
     float rho, lowpass, alpha_min, alpha_max, t_min, jac_clamp;
     float bg[3];
     float flag_eps; /* relative width of the borderline bands */
+    int32_t cell;   /* 0: every pixel walks every visible splat; > 0: pixel cells of cell x cell (see
+                       the cell index below) */
 } orc_config;
 
 /* Projected state of one splat in one view (FP64 except z32). */
@@ -296,13 +306,85 @@ static int32_t *visible_order(int n, const orc_splat *sp, int *n_vis) {
     return ord;
 }
 
+/* ------------------------------------------------------------ cell index
+ * The image is cut into cells of c x c pixels. Each cell lists, in the depth
+ * order of S5, every visible splat whose widened support box reaches a pixel
+ * centre of the cell. The support is Q <= qcut; the box of the ellipse
+ * Q <= q (Q = d^T Sigma'^-1 d) is |dx| <= sqrt(q Sigma'_00), |dy| <= sqrt(q Sigma'_11),
+ * taken here at q = qcut (1 + flag_eps) (1 + 1e-9) and widened by 1e-6 px. A
+ * splat that a pixel's cell does not list therefore has Q > qcut (1 + flag_eps)
+ * at that pixel: in the per-pixel loop it neither passes the support test nor
+ * sets the support-edge flag, so leaving it out changes nothing, and the loop
+ * over the cell's list gives the result of the loop over all splats bit for bit. */
+typedef struct {
+    int c, ncx, ncy;
+    size_t *start; /* ncx * ncy + 1 */
+    int32_t *ids;
+} orc_cells;
+
+static int cell_box(const orc_splat *s, const orc_camera *cam, double eps, int c, int *cx0, int *cx1, int *cy0,
+                    int *cy1) {
+    const double q = s->qcut * (1.0 + eps) * (1.0 + 1e-9);
+    const double ex = sqrt(s->S[0] * q) + 1e-6, ey = sqrt(s->S[2] * q) + 1e-6;
+    /* pixel x can be in the support iff |x + 0.5 - u| <= ex */
+    double x0 = ceil(s->u - ex - 0.5), x1 = floor(s->u + ex - 0.5);
+    double y0 = ceil(s->v - ey - 0.5), y1 = floor(s->v + ey - 0.5);
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > cam->width - 1) x1 = cam->width - 1;
+    if (y1 > cam->height - 1) y1 = cam->height - 1;
+    if (!(x0 <= x1 && y0 <= y1)) return 0;
+    *cx0 = (int)x0 / c; *cx1 = (int)x1 / c; *cy0 = (int)y0 / c; *cy1 = (int)y1 / c;
+    return 1;
+}
+
+static void build_cells(const int32_t *ord, int nv, const orc_splat *sp, const orc_camera *cam, double eps, int c,
+                        orc_cells *out) {
+    out->c = c;
+    out->ncx = (cam->width + c - 1) / c;
+    out->ncy = (cam->height + c - 1) / c;
+    const size_t nc = (size_t)out->ncx * out->ncy;
+    out->start = (size_t *)calloc(nc + 1, sizeof(size_t));
+    for (int k = 0; k < nv; ++k) {
+        int cx0, cx1, cy0, cy1;
+        if (!cell_box(&sp[ord[k]], cam, eps, c, &cx0, &cx1, &cy0, &cy1)) continue;
+        for (int cy = cy0; cy <= cy1; ++cy)
+            for (int cx = cx0; cx <= cx1; ++cx) out->start[(size_t)cy * out->ncx + cx + 1]++;
+    }
+    for (size_t i = 0; i < nc; ++i) out->start[i + 1] += out->start[i];
+    out->ids = (int32_t *)malloc(sizeof(int32_t) * (out->start[nc] > 0 ? out->start[nc] : 1));
+    size_t *fill = (size_t *)malloc(sizeof(size_t) * (nc > 0 ? nc : 1));
+    memcpy(fill, out->start, sizeof(size_t) * nc);
+    for (int k = 0; k < nv; ++k) { /* in depth order, so every list keeps it */
+        int cx0, cx1, cy0, cy1;
+        if (!cell_box(&sp[ord[k]], cam, eps, c, &cx0, &cx1, &cy0, &cy1)) continue;
+        for (int cy = cy0; cy <= cy1; ++cy)
+            for (int cx = cx0; cx <= cx1; ++cx) out->ids[fill[(size_t)cy * out->ncx + cx]++] = ord[k];
+    }
+    free(fill);
+}
+
+/* The splats pixel (x, y) walks: its cell's list, or all visible splats. */
+static const int32_t *pixel_list(const orc_cells *cells, const int32_t *ord, int nv, int x, int y, int *len) {
+    if (!cells) { *len = nv; return ord; }
+    const size_t ci = (size_t)(y / cells->c) * cells->ncx + (size_t)(x / cells->c);
+    *len = (int)(cells->start[ci + 1] - cells->start[ci]);
+    return cells->ids + cells->start[ci];
+}
+
+static void free_cells(orc_cells *cells) {
+    if (!cells) return;
+    free(cells->start);
+    free(cells->ids);
+}
+
 /* ------------------------------------------------------------ S6, one pixel */
 typedef struct {
     double color[3], depth, alpha, normal[3], T;
     int ncontrib, last_id, flags;
 } orc_pixel;
 
-enum { FLAG_SUPPORT = 1, FLAG_ALPHA_MIN = 2, FLAG_T_MIN = 4, FLAG_FACING = 8 };
+enum { FLAG_SUPPORT = 1, FLAG_ALPHA_MIN = 2, FLAG_T_MIN = 4, FLAG_FACING = 8, FLAG_CUSP = 16 };
 
 static double falloff(double Q, double beta) { return exp(-0.5 * pow(Q, 0.5 * beta)); }
 
@@ -331,6 +413,7 @@ static void render_pixel(const int32_t *ord, int nv, const orc_splat *sp, double
         D += w * s->z;
         for (int c = 0; c < 3; ++c) N[c] += w * s->normal[c];
         if (fabs(s->facing) <= eps) flags |= FLAG_FACING;
+        if (s->beta < 2.0 && dx * dx + dy * dy < 0.0625) flags |= FLAG_CUSP;
         T = Tn;
         ++cnt;
         last = ord[k];
@@ -386,16 +469,21 @@ int orc_render(int n, const double *pos_op, const double *lsb, const double *qua
     orc_splat *sp = project_all(n, pos_op, lsb, quat, color, cam, cfg);
     int nv;
     int32_t *ord = visible_order(n, sp, &nv);
+    orc_cells cells_, *cells = NULL;
+    if (cfg->cell > 0) { build_cells(ord, nv, sp, cam, cfg->flag_eps, cfg->cell, &cells_); cells = &cells_; }
 #pragma omp parallel for schedule(dynamic, 8)
     for (int p = 0; p < npix; ++p) {
         int x = pix ? pix[2 * p] : p % cam->width;
         int y = pix ? pix[2 * p + 1] : p / cam->width;
         orc_pixel o;
-        render_pixel(ord, nv, sp, x + 0.5, y + 0.5, cfg, &o);
+        int len;
+        const int32_t *lst = pixel_list(cells, ord, nv, x, y, &len);
+        render_pixel(lst, len, sp, x + 0.5, y + 0.5, cfg, &o);
         for (int c = 0; c < 3; ++c) { color_out[3 * p + c] = o.color[c]; normal_out[3 * p + c] = o.normal[c]; }
         depth_out[p] = o.depth; alpha_out[p] = o.alpha; T_out[p] = o.T;
         ncontrib[p] = o.ncontrib; last_id[p] = o.last_id; flags[p] = o.flags;
     }
+    free_cells(cells);
     free(ord);
     free(sp);
     return 0;
@@ -618,13 +706,18 @@ int orc_backward(int n, const double *pos_op, const double *lsb, const double *q
     int nv;
     int32_t *ord = visible_order(n, sp, &nv);
     double *g2d = (double *)calloc((size_t)16 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    orc_cells cells_, *cells = NULL;
+    if (cfg->cell > 0) { build_cells(ord, nv, sp, cam, cfg->flag_eps, cfg->cell, &cells_); cells = &cells_; }
 #pragma omp parallel for schedule(dynamic, 8)
     for (int p = 0; p < npix; ++p) {
         int x = pix ? pix[2 * p] : p % cam->width;
         int y = pix ? pix[2 * p + 1] : p / cam->width;
-        backward_pixel(ord, nv, sp, x + 0.5, y + 0.5, cfg, g_color + 3 * p, g_depth[p], g_alpha[p],
+        int len;
+        const int32_t *lst = pixel_list(cells, ord, nv, x, y, &len);
+        backward_pixel(lst, len, sp, x + 0.5, y + 0.5, cfg, g_color + 3 * p, g_depth[p], g_alpha[p],
                        g_normal + 3 * p, g2d);
     }
+    free_cells(cells);
     int K3 = 3 * n_sh_coeffs(cfg->sh_degree);
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {

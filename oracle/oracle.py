@@ -7,7 +7,8 @@ imports the CUDA path.
 Every function takes plain numpy arrays (any float dtype; converted to float64),
 a camera dict (width, height, fx, fy, cx, cy, viewmat (3, 4), znear) and a
 config dict (sh_degree, phi_mode, rho, lowpass, alpha_min, alpha_max, t_min,
-jac_clamp, bg, flag_eps). The arithmetic itself lives in the C file, which
+jac_clamp, bg, flag_eps, and optionally cell: walk a cell index of cell x cell pixels
+instead of every visible splat, bit-identical and far faster on large images). The arithmetic itself lives in the C file, which
 cites the paper's equations step by step.
 """
 from __future__ import annotations
@@ -52,7 +53,7 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("sh_degree", ctypes.c_int32), ("phi_mode", ctypes.c_int32), ("rho", ctypes.c_float),
                 ("lowpass", ctypes.c_float), ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("t_min", ctypes.c_float), ("jac_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3),
-                ("flag_eps", ctypes.c_float)]
+                ("flag_eps", ctypes.c_float), ("cell", ctypes.c_int32)]
 
 
 def _load():
@@ -92,6 +93,7 @@ def _cfg(c: dict, sh_degree: int) -> _Cfg:
     for i in range(3):
         cfg.bg[i] = float(c["bg"][i])
     cfg.flag_eps = float(c.get("flag_eps", 1e-4))
+    cfg.cell = int(c.get("cell", 0))
     return cfg
 
 

@@ -417,3 +417,41 @@ def test_tile_lists_cover_the_exact_support():
             assert (py // th) * tiles_x + px // tw in tiles
         checked += len(inside)
     assert checked > 1000
+
+
+# ---------------------------------------------------------------- the oracle's cell index
+@pytest.mark.parametrize("kind,sh,cell", [("object", 3, 1), ("object", 3, 7), ("uniform", -1, 16), ("uniform", -1, 64)])
+def test_cell_index_gives_the_brute_force_result(kind, sh, cell):
+    """Walking a pixel's cell list instead of every visible splat leaves out only splats whose step
+    of the per-pixel loop does nothing, so the forward (every output and flag) is identical bit for
+    bit, and the gradient equal up to the order of its FP64 sums. The uniform scene has splats
+    whose boxes cover many cells and reach past the image border."""
+    sc = make_scene(2500, 17, kind, sh)
+    cam = look_at((0.4, -2.6, 0.9), (0, 0, 0), 203, 151).as_dict()
+    base = oracle_cfg()
+    ref = O.render(sc, cam, base)
+    got = O.render(sc, cam, dict(base, cell=cell))
+    for k in ref:
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+    assert (ref["n_contrib"] > 0).mean() > 0.3  # the scene covers the image
+    rng = np.random.default_rng(cell)
+    P = cam["width"] * cam["height"]
+    g = [rng.standard_normal((P, 3)), rng.standard_normal(P), rng.standard_normal(P), rng.standard_normal((P, 3))]
+    gb = O.backward(sc, cam, base, *g)
+    gc = O.backward(sc, cam, dict(base, cell=cell), *g)
+    for k in ("g2d", "g_pos_op", "g_lscale_beta", "g_quat", "g_color"):
+        np.testing.assert_allclose(gc[k], gb[k], rtol=1e-11, atol=1e-11 * np.abs(gb[k]).max(), err_msg=k)
+
+
+def test_cusp_flag_marks_pixels_near_the_centre_of_a_low_beta_splat():
+    """Reading D16: a blended splat with beta < 2 whose centre lies within 0.25 px of a pixel's
+    sample point flags that pixel; beta >= 2, or farther away, does not."""
+    cam = axis_camera(9, 9, 40.0)
+    for beta, off, flagged in ((1.5, 0.1, True), (1.5, 0.3, False), (2.0, 0.1, False), (3.0, 0.0, False)):
+        # centre at x = 4.5 + off px, y = 4.5 px (pixel (4, 4)'s sample point), depth 2
+        u = (4.5 + off - 4.5) * 2.0 / 40.0
+        sc = make_splats([[u, 0.0, 2.0]], [-3.0, -3.0, -3.0], beta, 0.8)
+        out = O.render(sc, cam, oracle_cfg())
+        f = out["flags"].reshape(9, 9)[4, 4]
+        assert bool(f & O.FLAG_CUSP) == flagged, (beta, off, f)
+        assert out["n_contrib"].reshape(9, 9)[4, 4] == 1
