@@ -85,7 +85,8 @@ typedef enum ges_status {
     GES_ERR_INVALID_ARG = 1, /* host-side check failed; nothing was launched */
     GES_ERR_CAPACITY = 2,    /* more tile instances than `bins` holds; lists were truncated */
     GES_ERR_CUDA = 3,        /* a CUDA launch or copy failed */
-    GES_ERR_NUMERIC = 4,     /* a visible splat had a non-finite projection; it was culled */
+    GES_ERR_NUMERIC = 4,     /* a splat had a non-finite position, opacity or beta, a beta <= 0, or (if
+                                visible) a non-finite projection; it was culled */
     GES_ERR_TOO_LARGE = 5    /* the problem exceeds the fixed scratch of ges_render_bwd_noalloc */
 } ges_status;
 

@@ -69,6 +69,9 @@ typedef struct {
     float flag_eps; /* relative width of the borderline bands */
     int32_t cell;   /* 0: every pixel walks every visible splat; > 0: pixel cells of cell x cell (see
                        the cell index below) */
+    float shift[2]; /* offset of the sample points from the pixel centres (0, 0 for the method; the
+                       parity tests move them by the float32 rounding of the screen centres to see
+                       how far the gradient moves with it) */
 } orc_config;
 
 /* Projected state of one splat in one view (FP64 except z32). */
@@ -84,6 +87,7 @@ typedef struct {
     double rgb[3];
     double normal[3];
     double facing; /* n . (campos - mu) / |campos - mu| before the sign flip */
+    double du, dv; /* bound on the float32 rounding of (u, v) on the GPU side (pixels), for the flags */
 } orc_splat;
 
 /* ------------------------------------------------------------------ helpers */
@@ -244,6 +248,18 @@ static void project_splat(const double *pos_op, const double *lsb, const double 
     s->u = fx * t[0] / t[2] + cam->cx;
     s->v = fy * t[1] / t[2] + cam->cy;
     s->z = t[2];
+    /* First-order bound on the float32 rounding of u, v as the GPU computes them (t_i as a
+       float32 dot product plus translation, then fx t_x / t_z + c_x): each t_i carries at most
+       2^-22 (sum_j |W_ij mu_j| + |t_i|), and u carries fx (e_x + |t_x / t_z| e_z) / t_z plus
+       2^-22 (|u| + |u - c_x|) from its own operations. Only the borderline flags use it. */
+    {
+        double et[3];
+        for (int i = 0; i < 3; ++i)
+            et[i] = ldexp(fabs(W[i * 3 + 0] * mu[0]) + fabs(W[i * 3 + 1] * mu[1]) + fabs(W[i * 3 + 2] * mu[2]) +
+                          fabs(tw[i]), -22);
+        s->du = fx * (et[0] + fabs(t[0] / t[2]) * et[2]) / t[2] + ldexp(fabs(s->u) + fabs(s->u - cam->cx), -22);
+        s->dv = fy * (et[1] + fabs(t[1] / t[2]) * et[2]) / t[2] + ldexp(fabs(s->v) + fabs(s->v - cam->cy), -22);
+    }
 
     /* S3: exact support of exp(-1/2 Q^(beta/2)) >= alpha_min / o */
     s->qcut = pow(2.0 * log(op / (double)cfg->alpha_min), 2.0 / beta);
@@ -309,24 +325,33 @@ static int32_t *visible_order(int n, const orc_splat *sp, int *n_vis) {
 /* ------------------------------------------------------------ cell index
  * The image is cut into cells of c x c pixels. Each cell lists, in the depth
  * order of S5, every visible splat whose widened support box reaches a pixel
- * centre of the cell. The support is Q <= qcut; the box of the ellipse
- * Q <= q (Q = d^T Sigma'^-1 d) is |dx| <= sqrt(q Sigma'_00), |dy| <= sqrt(q Sigma'_11),
- * taken here at q = qcut (1 + flag_eps) (1 + 1e-9) and widened by 1e-6 px. A
- * splat that a pixel's cell does not list therefore has Q > qcut (1 + flag_eps)
- * at that pixel: in the per-pixel loop it neither passes the support test nor
- * sets the support-edge flag, so leaving it out changes nothing, and the loop
- * over the cell's list gives the result of the loop over all splats bit for bit. */
+ * centre of the cell. A splat changes a pixel's loop only where it passes the
+ * support test (Q <= qcut) or sets the support-edge flag, Q <= q* + dQ with
+ * q* = qcut (1 + flag_eps) and dQ as in render_pixel. With r = sqrt(Q), |C d| <=
+ * sqrt(lam) r (lam the largest eigenvalue of the conic C) and
+ * dQ <= 2 sqrt2 delta |C d| + 2^-20 Q (delta = max(du, dv)), both need
+ * r (1 - 2^-20) r - 2 sqrt2 delta sqrt(lam) r - q* <= 0, i.e. r <= r_max. The box
+ * of the ellipse Q <= q (Q = d^T Sigma'^-1 d) is |dx| <= sqrt(q Sigma'_00),
+ * |dy| <= sqrt(q Sigma'_11), taken at q = r_max^2 (1 + 1e-9) and widened by
+ * 1e-6 px. A splat that a pixel's cell does not list is therefore a no-op step
+ * of that pixel's loop, and the loop over the cell's list gives the result of
+ * the loop over all splats bit for bit. */
 typedef struct {
     int c, ncx, ncy;
     size_t *start; /* ncx * ncy + 1 */
     int32_t *ids;
 } orc_cells;
 
-static int cell_box(const orc_splat *s, const orc_camera *cam, double eps, int c, int *cx0, int *cx1, int *cy0,
-                    int *cy1) {
-    const double q = s->qcut * (1.0 + eps) * (1.0 + 1e-9);
-    const double ex = sqrt(s->S[0] * q) + 1e-6, ey = sqrt(s->S[2] * q) + 1e-6;
-    /* pixel x can be in the support iff |x + 0.5 - u| <= ex */
+static int cell_box(const orc_splat *s, const orc_camera *cam, double eps, const float shift[2], int c, int *cx0,
+                    int *cx1, int *cy0, int *cy1) {
+    const double c0 = s->conic[0], c1 = s->conic[1], c2 = s->conic[2];
+    const double lam = 0.5 * (c0 + c2) + sqrt(0.25 * (c0 - c2) * (c0 - c2) + c1 * c1);
+    const double dl = s->du > s->dv ? s->du : s->dv, k = 1.0 - ldexp(1.0, -20);
+    const double rmax = (sqrt(2.0 * lam) * dl + sqrt(2.0 * lam * dl * dl + k * s->qcut * (1.0 + eps))) / k;
+    const double q = rmax * rmax * (1.0 + 1e-9);
+    const double ex = sqrt(s->S[0] * q) + 1e-6 + fabs(shift[0]), ey = sqrt(s->S[2] * q) + 1e-6 + fabs(shift[1]);
+    /* pixel x (sampled at x + 0.5 + shift, |shift| added to ex above) can be in the support iff
+       |x + 0.5 - u| <= ex */
     double x0 = ceil(s->u - ex - 0.5), x1 = floor(s->u + ex - 0.5);
     double y0 = ceil(s->v - ey - 0.5), y1 = floor(s->v + ey - 0.5);
     if (x0 < 0) x0 = 0;
@@ -338,8 +363,8 @@ static int cell_box(const orc_splat *s, const orc_camera *cam, double eps, int c
     return 1;
 }
 
-static void build_cells(const int32_t *ord, int nv, const orc_splat *sp, const orc_camera *cam, double eps, int c,
-                        orc_cells *out) {
+static void build_cells(const int32_t *ord, int nv, const orc_splat *sp, const orc_camera *cam, double eps,
+                        const float shift[2], int c, orc_cells *out) {
     out->c = c;
     out->ncx = (cam->width + c - 1) / c;
     out->ncy = (cam->height + c - 1) / c;
@@ -347,7 +372,7 @@ static void build_cells(const int32_t *ord, int nv, const orc_splat *sp, const o
     out->start = (size_t *)calloc(nc + 1, sizeof(size_t));
     for (int k = 0; k < nv; ++k) {
         int cx0, cx1, cy0, cy1;
-        if (!cell_box(&sp[ord[k]], cam, eps, c, &cx0, &cx1, &cy0, &cy1)) continue;
+        if (!cell_box(&sp[ord[k]], cam, eps, shift, c, &cx0, &cx1, &cy0, &cy1)) continue;
         for (int cy = cy0; cy <= cy1; ++cy)
             for (int cx = cx0; cx <= cx1; ++cx) out->start[(size_t)cy * out->ncx + cx + 1]++;
     }
@@ -357,7 +382,7 @@ static void build_cells(const int32_t *ord, int nv, const orc_splat *sp, const o
     memcpy(fill, out->start, sizeof(size_t) * nc);
     for (int k = 0; k < nv; ++k) { /* in depth order, so every list keeps it */
         int cx0, cx1, cy0, cy1;
-        if (!cell_box(&sp[ord[k]], cam, eps, c, &cx0, &cx1, &cy0, &cy1)) continue;
+        if (!cell_box(&sp[ord[k]], cam, eps, shift, c, &cx0, &cx1, &cy0, &cy1)) continue;
         for (int cy = cy0; cy <= cy1; ++cy)
             for (int cx = cx0; cx <= cx1; ++cx) out->ids[fill[(size_t)cy * out->ncx + cx]++] = ord[k];
     }
@@ -388,9 +413,16 @@ enum { FLAG_SUPPORT = 1, FLAG_ALPHA_MIN = 2, FLAG_T_MIN = 4, FLAG_FACING = 8, FL
 
 static double falloff(double Q, double beta) { return exp(-0.5 * pow(Q, 0.5 * beta)); }
 
+/* Borderline bands. A decision is flagged when float32 may take it the other way: Q against
+ * qcut within eps qcut plus dQ, the change of Q under the float32 rounding (du, dv) of the
+ * splat's screen centre, dQ = 2 (|m_x| du + |m_y| dv) with m = C d, plus 2^-20 Q for the conic's
+ * own rounding; alpha against alpha_min within eps alpha_min plus the matching d alpha =
+ * alpha (beta / 4) p dQ / Q; the transmittance against t_min within (eps + rT) t_min, rT the
+ * relative error it has gathered: sum of d alpha / (1 - alpha) over the blended splats and
+ * 2^-21 (1 + p) for each one's float32 falloff and product. */
 static void render_pixel(const int32_t *ord, int nv, const orc_splat *sp, double px, double py,
                          const orc_config *cfg, orc_pixel *out) {
-    double T = 1.0, C[3] = {0, 0, 0}, D = 0, N[3] = {0, 0, 0};
+    double T = 1.0, C[3] = {0, 0, 0}, D = 0, N[3] = {0, 0, 0}, rT = 0.0;
     int cnt = 0, last = -1, flags = 0;
     const double eps = cfg->flag_eps;
     const double amin = cfg->alpha_min, amax = cfg->alpha_max, tmin = cfg->t_min;
@@ -398,16 +430,22 @@ static void render_pixel(const int32_t *ord, int nv, const orc_splat *sp, double
         const orc_splat *s = &sp[ord[k]];
         double dx = px - s->u, dy = py - s->v;
         double Q = s->conic[0] * dx * dx + 2.0 * s->conic[1] * dx * dy + s->conic[2] * dy * dy;
-        if (fabs(Q - s->qcut) <= eps * s->qcut) flags |= FLAG_SUPPORT;
+        const double mx = s->conic[0] * dx + s->conic[1] * dy, my = s->conic[1] * dx + s->conic[2] * dy;
+        const double dQ = 2.0 * (fabs(mx) * s->du + fabs(my) * s->dv) + ldexp(fabs(Q), -20);
+        if (fabs(Q - s->qcut) <= eps * s->qcut + dQ) flags |= FLAG_SUPPORT;
         if (Q > s->qcut) continue;
         double G = falloff(Q, s->beta);
         double a = s->opacity * G;
         if (a > amax) a = amax;
-        if (fabs(a - amin) <= eps * amin) flags |= FLAG_ALPHA_MIN;
+        const double p = pow(Q, 0.5 * s->beta);
+        const double da = Q > 0 ? a * 0.25 * s->beta * p * dQ / Q : 0.0;
+        if (fabs(a - amin) <= eps * amin + da) flags |= FLAG_ALPHA_MIN;
         if (a < amin) continue;
         double Tn = T * (1.0 - a);
-        if (fabs(Tn - tmin) <= eps * tmin) flags |= FLAG_T_MIN;
+        const double rTn = rT + da / (1.0 - a) + ldexp(1.0 + p, -21);
+        if (fabs(Tn - tmin) <= (eps + rTn) * tmin) flags |= FLAG_T_MIN;
         if (Tn < tmin) break;
+        rT = rTn;
         double w = a * T;
         for (int c = 0; c < 3; ++c) C[c] += w * s->rgb[c];
         D += w * s->z;
@@ -432,7 +470,7 @@ static void render_pixel(const int32_t *ord, int nv, const orc_splat *sp, double
 int orc_preprocess(int n, const double *pos_op, const double *lsb, const double *quat, const double *color,
                    const orc_camera *cam, const orc_config *cfg,
                    int32_t *visible, float *z32, double *uvz, double *cov2d, double *conic, double *qcut,
-                   double *rgb, double *normal) {
+                   double *rgb, double *normal, double *duv) {
     int K3 = 3 * n_sh_coeffs(cfg->sh_degree);
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
@@ -446,6 +484,7 @@ int orc_preprocess(int n, const double *pos_op, const double *lsb, const double 
             rgb[3 * i + j] = s.rgb[j]; normal[3 * i + j] = s.normal[j];
         }
         qcut[i] = s.qcut;
+        if (duv) { duv[2 * i] = s.du; duv[2 * i + 1] = s.dv; }
     }
     return 0;
 }
@@ -470,7 +509,7 @@ int orc_render(int n, const double *pos_op, const double *lsb, const double *qua
     int nv;
     int32_t *ord = visible_order(n, sp, &nv);
     orc_cells cells_, *cells = NULL;
-    if (cfg->cell > 0) { build_cells(ord, nv, sp, cam, cfg->flag_eps, cfg->cell, &cells_); cells = &cells_; }
+    if (cfg->cell > 0) { build_cells(ord, nv, sp, cam, cfg->flag_eps, cfg->shift, cfg->cell, &cells_); cells = &cells_; }
 #pragma omp parallel for schedule(dynamic, 8)
     for (int p = 0; p < npix; ++p) {
         int x = pix ? pix[2 * p] : p % cam->width;
@@ -478,7 +517,7 @@ int orc_render(int n, const double *pos_op, const double *lsb, const double *qua
         orc_pixel o;
         int len;
         const int32_t *lst = pixel_list(cells, ord, nv, x, y, &len);
-        render_pixel(lst, len, sp, x + 0.5, y + 0.5, cfg, &o);
+        render_pixel(lst, len, sp, x + 0.5 + cfg->shift[0], y + 0.5 + cfg->shift[1], cfg, &o);
         for (int c = 0; c < 3; ++c) { color_out[3 * p + c] = o.color[c]; normal_out[3 * p + c] = o.normal[c]; }
         depth_out[p] = o.depth; alpha_out[p] = o.alpha; T_out[p] = o.T;
         ncontrib[p] = o.ncontrib; last_id[p] = o.last_id; flags[p] = o.flags;
@@ -707,14 +746,14 @@ int orc_backward(int n, const double *pos_op, const double *lsb, const double *q
     int32_t *ord = visible_order(n, sp, &nv);
     double *g2d = (double *)calloc((size_t)16 * (size_t)(n > 0 ? n : 1), sizeof(double));
     orc_cells cells_, *cells = NULL;
-    if (cfg->cell > 0) { build_cells(ord, nv, sp, cam, cfg->flag_eps, cfg->cell, &cells_); cells = &cells_; }
+    if (cfg->cell > 0) { build_cells(ord, nv, sp, cam, cfg->flag_eps, cfg->shift, cfg->cell, &cells_); cells = &cells_; }
 #pragma omp parallel for schedule(dynamic, 8)
     for (int p = 0; p < npix; ++p) {
         int x = pix ? pix[2 * p] : p % cam->width;
         int y = pix ? pix[2 * p + 1] : p / cam->width;
         int len;
         const int32_t *lst = pixel_list(cells, ord, nv, x, y, &len);
-        backward_pixel(lst, len, sp, x + 0.5, y + 0.5, cfg, g_color + 3 * p, g_depth[p], g_alpha[p],
+        backward_pixel(lst, len, sp, x + 0.5 + cfg->shift[0], y + 0.5 + cfg->shift[1], cfg, g_color + 3 * p, g_depth[p], g_alpha[p],
                        g_normal + 3 * p, g2d);
     }
     free_cells(cells);

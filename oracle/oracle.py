@@ -8,7 +8,8 @@ Every function takes plain numpy arrays (any float dtype; converted to float64),
 a camera dict (width, height, fx, fy, cx, cy, viewmat (3, 4), znear) and a
 config dict (sh_degree, phi_mode, rho, lowpass, alpha_min, alpha_max, t_min,
 jac_clamp, bg, flag_eps, and optionally cell: walk a cell index of cell x cell pixels
-instead of every visible splat, bit-identical and far faster on large images). The arithmetic itself lives in the C file, which
+instead of every visible splat, bit-identical and far faster on large images; shift: (dx, dy)
+offset of the sample points from the pixel centres, (0, 0) for the method). The arithmetic itself lives in the C file, which
 cites the paper's equations step by step.
 """
 from __future__ import annotations
@@ -53,7 +54,7 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("sh_degree", ctypes.c_int32), ("phi_mode", ctypes.c_int32), ("rho", ctypes.c_float),
                 ("lowpass", ctypes.c_float), ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("t_min", ctypes.c_float), ("jac_clamp", ctypes.c_float), ("bg", ctypes.c_float * 3),
-                ("flag_eps", ctypes.c_float), ("cell", ctypes.c_int32)]
+                ("flag_eps", ctypes.c_float), ("cell", ctypes.c_int32), ("shift", ctypes.c_float * 2)]
 
 
 def _load():
@@ -62,7 +63,7 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build_oracle())
             P = ctypes.c_void_p
-            lib.orc_preprocess.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
+            lib.orc_preprocess.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
             lib.orc_render.argtypes = [ctypes.c_int, P, P, P, P, P, P, ctypes.c_int, P, P, P, P, P, P, P, P, P]
             lib.orc_backward.argtypes = [ctypes.c_int, P, P, P, P, P, P, ctypes.c_int, P, P, P, P, P, P, P, P,
                                          P, P]
@@ -94,6 +95,8 @@ def _cfg(c: dict, sh_degree: int) -> _Cfg:
         cfg.bg[i] = float(c["bg"][i])
     cfg.flag_eps = float(c.get("flag_eps", 1e-4))
     cfg.cell = int(c.get("cell", 0))
+    sh = c.get("shift", (0.0, 0.0))
+    cfg.shift[0], cfg.shift[1] = float(sh[0]), float(sh[1])
     return cfg
 
 
@@ -110,17 +113,18 @@ def _arrays(scene):
 
 
 def preprocess(scene, cam: dict, cfg: dict) -> dict:
-    """Per-splat projection of S1-S4 (FP64; z32 is the float32 sort depth)."""
+    """Per-splat projection of S1-S4 (FP64; z32 is the float32 sort depth), and duv: the bound on
+    the float32 rounding of (u, v) that the borderline flags use."""
     lib = _load()
     pos, lsb, q, col = _arrays(scene)
     n = pos.shape[0]
     out = dict(visible=np.zeros(n, np.int32), z32=np.zeros(n, np.float32), uvz=np.zeros((n, 3)),
                cov2d=np.zeros((n, 3)), conic=np.zeros((n, 3)), qcut=np.zeros(n), rgb=np.zeros((n, 3)),
-               normal=np.zeros((n, 3)))
+               normal=np.zeros((n, 3)), duv=np.zeros((n, 2)))
     c, g = _cam(cam), _cfg(cfg, scene.sh_degree)
     lib.orc_preprocess(n, _p(pos), _p(lsb), _p(q), _p(col), ctypes.byref(c), ctypes.byref(g),
                        _p(out["visible"]), _p(out["z32"]), _p(out["uvz"]), _p(out["cov2d"]), _p(out["conic"]),
-                       _p(out["qcut"]), _p(out["rgb"]), _p(out["normal"]))
+                       _p(out["qcut"]), _p(out["rgb"]), _p(out["normal"]), _p(out["duv"]))
     return out
 
 

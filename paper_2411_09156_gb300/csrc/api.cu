@@ -129,7 +129,7 @@ const char *ges_status_string(ges_status s) {
         case GES_ERR_INVALID_ARG: return "invalid argument";
         case GES_ERR_CAPACITY: return "tile-instance capacity exceeded; lists truncated";
         case GES_ERR_CUDA: return "CUDA error";
-        case GES_ERR_NUMERIC: return "non-finite projection; splat culled";
+        case GES_ERR_NUMERIC: return "non-finite input or projection; splat culled";
         case GES_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of the no-allocation entry point";
         default: return "unknown status";
     }

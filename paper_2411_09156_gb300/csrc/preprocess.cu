@@ -118,9 +118,12 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {
         const float *vm = a.V.vm[v];
         z32 = depth32(vm, po.x, po.y, po.z);
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+        // a splat with a non-finite position, opacity or shape, or beta <= 0, is culled and reported
+        const bool in_ok = isfinite(po.x) && isfinite(po.y) && isfinite(po.z) && isfinite(o) && isfinite(beta) &&
+                           beta > 0.f;
+        if (!in_ok) set_error(a.err, kErrNumeric);
         const bool op_ok = o >= a.P.alpha_min;
-        visible = op_ok && isfinite(po.x) && isfinite(po.y) && isfinite(po.z) && isfinite(beta) && beta > 0.f &&
-                  z32 > a.V.znear[v];
+        visible = in_ok && op_ok && z32 > a.V.znear[v];
         if (visible) {
             const float qinv = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
             float R[9];
@@ -478,7 +481,15 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(PreBwdArgs a) {
     for (int k = 0; k < 9; ++k) GR[k] = seg_sum(GR[k], seg);
     gop = seg_sum(gop, seg);
     gbeta = seg_sum(gbeta, seg);
-    if (splat_ok && v == 0) {
+    // a splat with no screen-space gradient in any view (culled, or reaching no pixel with an
+    // upstream gradient) has zero 3-D gradients, whatever its parameters (a culled splat may hold
+    // non-finite ones)
+    const bool any_view = seg_sum(has ? 1.f : 0.f, seg) > 0.f;
+    if (splat_ok && v == 0 && !any_view) {
+        a.g_quat[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.g_pos_op[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.g_lsb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else if (splat_ok && v == 0) {
         // s'_k = phi(beta) exp(l_k): dL/dl_k = 2 s'_k^2 gD_k, dL/dbeta += 2 s'_k gD_k phi'(beta) exp(l_k)
         float gl[3];
 #pragma unroll

@@ -11,10 +11,12 @@ IMG_ATOL = 2e-4
 GRAD_REL_L2 = 1e-3
 
 
-def oracle_cfg(cfg: api.GESConfig, flag_eps=1e-4) -> dict:
+def oracle_cfg(cfg: api.GESConfig, flag_eps=1e-4, cell=16) -> dict:
+    """The oracle's config for a GESConfig; cell: the oracle's pixel-cell index (bit-identical to
+    its brute-force loop, pinned in tests/test_oracle_pins.py), 0 for the brute-force loop."""
     return dict(phi_mode=cfg.phi_mode, rho=cfg.rho, lowpass=cfg.lowpass, alpha_min=cfg.alpha_min,
                 alpha_max=cfg.alpha_max, t_min=cfg.t_min, jac_clamp=cfg.jac_clamp, bg=tuple(cfg.bg),
-                flag_eps=flag_eps)
+                flag_eps=flag_eps, cell=cell)
 
 
 def gpu_forward(scene, cams, cfg: api.GESConfig, **kw):
@@ -54,7 +56,11 @@ def compare_forward(rast, scene, cams, cfg, v=0, pixels=None, atol=IMG_ATOL):
     for k in ("color", "depth", "alpha", "normal"):
         err = np.abs(got[k][mask] - ref[k][mask])
         rep[k] = float(err.max()) if err.size else 0.0
-        assert rep[k] <= atol, (k, rep[k])
+        if err.size and rep[k] > atol:  # the worst pixel, for the report
+            j = np.nonzero(mask)[0][np.argmax(err.reshape(err.shape[0], -1).max(1))]
+            rep["worst"] = dict(index=int(j), got=np.asarray(got[k][j]).tolist(), ref=np.asarray(ref[k][j]).tolist(),
+                                n_contrib=int(ref["n_contrib"][j]), T=float(ref["T"][j]), flags=int(ref["flags"][j]))
+        assert rep[k] <= atol, (k, rep[k], rep.get("worst"))
     np.testing.assert_array_equal(got["n_contrib"][mask], ref["n_contrib"][mask])
     # last contributor: splat id of the instance before `last`
     n_inst = rast.capacity
@@ -119,7 +125,7 @@ def oracle_upstream(rast, grads, v, pixels=None):
 GRAD_REPORT = []
 
 
-def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=3e-3, floor=0.25, rows=None):
+def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=3e-3, floor=0.25, rows=None, sens=None):
     """Tensor-level relative L2 <= 1e-3 (the gradient tolerance) and, as a guard against a wrong
     formula for a single parameter, elementwise |d| <= elem * max(|g|, floor * rms(g)).
 
@@ -128,7 +134,13 @@ def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=3e-3, floor=0.2
     prefix sum, so a splat deep in a pixel's list (T_i ~ 1e-4) carries an absolute
     error of a few ulp of the final value, i.e. a relative error up to ~1e-3 of its
     own small gradient. Each call also records the error in the tighter form
-    |d| / max(|g|, 1e-2 rms(g)) in GRAD_REPORT."""
+    |d| / max(|g|, 1e-2 rms(g)) in GRAD_REPORT.
+
+    sens (optional, per tensor, the shape of the gradient): how far the oracle's gradient moves when
+    its sample points move by the float32 rounding of the splats' screen centres (see
+    sensitivity()); the elementwise bounds then allow 2 sens more. A position gradient is a sum
+    over pixels whose terms largely cancel, so that rounding, tiny per pixel, can move it by
+    more than 3e-3 of itself."""
     import os
     rep = {}
     test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
@@ -141,16 +153,46 @@ def compare_grads(got: dict, ref: dict, rel_l2=GRAD_REL_L2, elem=3e-3, floor=0.2
         r = float(np.linalg.norm(a - b) / max(den, 1e-30))
         rms = float(np.sqrt(np.mean(b * b))) if b.size else 0.0
         d = np.abs(a - b)
-        bad = d > elem * np.maximum(np.abs(b), floor * rms)
+        sv = 0.0
+        if sens is not None:
+            sv = np.asarray(sens[k], np.float64).reshape(len(sens[k]), -1)
+            sv = sv[rows] if rows is not None else sv
+        bad = d > elem * np.maximum(np.abs(b), floor * rms) + 2.0 * sv
         tight = d / np.maximum(np.maximum(np.abs(b), 1e-2 * rms), 1e-30)
+        tight_s = d / np.maximum(1e-3 * np.maximum(np.abs(b), 1e-2 * rms) + 2.0 * sv, 1e-30)
         rep[k] = dict(rel_l2=r, max_abs=float(d.max()) if a.size else 0.0, n_bad=int(bad.sum()),
                       tight_max=float(tight.max()) if a.size else 0.0, tight_over=int((tight > 1e-3).sum()),
+                      tight_sens_max=float(tight_s.max()) if a.size else 0.0, sens=sens is not None,
                       guard_max=float((d / np.maximum(np.maximum(np.abs(b), floor * rms), 1e-30)).max())
                       if a.size else 0.0, n=int(a.size))
+        if a.size:
+            w = np.unravel_index(np.argmax(d / np.maximum(np.maximum(np.abs(b), floor * rms), 1e-30)), d.shape)
+            rep[k]["worst"] = dict(row=int(w[0]) if rows is None else int(np.asarray(rows)[w[0]]), col=int(w[1]),
+                                   got=float(a[w]), ref=float(b[w]), rms=rms)
         GRAD_REPORT.append(dict(test=test, tensor=k, **rep[k]))
         assert r <= rel_l2, (k, rep[k])
         assert bad.sum() == 0, (k, rep[k])
     return rep
+
+
+def sensitivity(sc, cams, cfg, per_view):
+    """Per-element sensitivity of the oracle's gradient to the float32 rounding of the screen
+    centres: |g(shift (d, 0)) - g| + |g(shift (0, d)) - g|, summed over the views, with d the
+    largest bound (du, dv) of the view's visible splats. per_view: {v: (pixels, (oc, od, oa, on),
+    g)}, g the unshifted oracle gradient of view v."""
+    from oracle import oracle as O
+    out = None
+    for v, (px, up, g0) in per_view.items():
+        cam = cams[v].as_dict()
+        pre = O.preprocess(sc, cam, oracle_cfg(cfg))
+        d = float(pre["duv"][pre["visible"] == 1].max()) if (pre["visible"] == 1).any() else 0.0
+        acc = {k: np.zeros_like(g0[k]) for k in ("g_pos_op", "g_lscale_beta", "g_quat", "g_color")}
+        for shift in ((d, 0.0), (0.0, d)):
+            gs = O.backward(sc, cam, dict(oracle_cfg(cfg), shift=shift), *up, pixels=px)
+            for k in acc:
+                acc[k] += np.abs(gs[k] - g0[k])
+        out = acc if out is None else {k: out[k] + acc[k] for k in out}
+    return out
 
 
 def oracle_g2d_sigma(g2d, conic):

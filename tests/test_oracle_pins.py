@@ -420,14 +420,17 @@ def test_tile_lists_cover_the_exact_support():
 
 
 # ---------------------------------------------------------------- the oracle's cell index
-@pytest.mark.parametrize("kind,sh,cell", [("object", 3, 1), ("object", 3, 7), ("uniform", -1, 16), ("uniform", -1, 64)])
-def test_cell_index_gives_the_brute_force_result(kind, sh, cell):
+@pytest.mark.parametrize("kind,sh,cell,w,h", [("object", 3, 1, 203, 151), ("object", 3, 7, 203, 151),
+                                              ("uniform", -1, 16, 203, 151), ("uniform", -1, 64, 203, 151),
+                                              ("object", 3, 16, 1600, 1040)])
+def test_cell_index_gives_the_brute_force_result(kind, sh, cell, w, h):
     """Walking a pixel's cell list instead of every visible splat leaves out only splats whose step
     of the per-pixel loop does nothing, so the forward (every output and flag) is identical bit for
     bit, and the gradient equal up to the order of its FP64 sums. The uniform scene has splats
-    whose boxes cover many cells and reach past the image border."""
+    whose boxes cover many cells and reach past the image border; at 1600x1040 the borderline
+    bands, which grow with the float32 rounding of the screen centres, are widest."""
     sc = make_scene(2500, 17, kind, sh)
-    cam = look_at((0.4, -2.6, 0.9), (0, 0, 0), 203, 151).as_dict()
+    cam = look_at((0.4, -2.6, 0.9), (0, 0, 0), w, h).as_dict()
     base = oracle_cfg()
     ref = O.render(sc, cam, base)
     got = O.render(sc, cam, dict(base, cell=cell))
@@ -443,6 +446,21 @@ def test_cell_index_gives_the_brute_force_result(kind, sh, cell):
         np.testing.assert_allclose(gc[k], gb[k], rtol=1e-11, atol=1e-11 * np.abs(gb[k]).max(), err_msg=k)
 
 
+def test_sample_shift_moves_the_sample_point():
+    """The shift of the sample points moves them relative to the splats: a single splat rendered
+    with the sample points shifted by (sx, sy) equals the splat moved by (-sx, -sy) on screen
+    (here by moving it in the world along the image axes of an axis-aligned camera; its extent
+    along z is negligible, so the projected covariance does not depend on where it sits)."""
+    cam = axis_camera(31, 23, 40.0)
+    cfg = oracle_cfg()
+    sx, sy, Z = 0.3, -0.2, 2.0
+    a = O.render(make_splats([[0.05, -0.02, Z]], [-2.5, -2.8, -14.0], 2.7, 0.7), cam, dict(cfg, shift=(sx, sy)))
+    b = O.render(make_splats([[0.05 - sx * Z / 40.0, -0.02 - sy * Z / 40.0, Z]], [-2.5, -2.8, -14.0], 2.7, 0.7),
+                 cam, cfg)
+    np.testing.assert_allclose(a["color"], b["color"], atol=1e-9)
+    np.testing.assert_array_equal(a["n_contrib"], b["n_contrib"])
+
+
 def test_cusp_flag_marks_pixels_near_the_centre_of_a_low_beta_splat():
     """Reading D16: a blended splat with beta < 2 whose centre lies within 0.25 px of a pixel's
     sample point flags that pixel; beta >= 2, or farther away, does not."""
@@ -455,3 +473,43 @@ def test_cusp_flag_marks_pixels_near_the_centre_of_a_low_beta_splat():
         f = out["flags"].reshape(9, 9)[4, 4]
         assert bool(f & O.FLAG_CUSP) == flagged, (beta, off, f)
         assert out["n_contrib"].reshape(9, 9)[4, 4] == 1
+
+
+def test_cell_index_keeps_a_splat_whose_support_band_flags_a_pixel_past_its_box():
+    """A splat whose support-edge band (which widens with the float32 rounding of its screen
+    centre, about 4e-4 px on a 1601-px view) reaches a pixel centre just beyond the box of
+    Q <= qcut (1 + flag_eps): the brute-force loop flags that pixel, so the cell index must list
+    the splat there too. The splat is axis-aligned on the centre row of an odd-height view; its
+    x is solved so that its box edge falls 1e-4 px short of the pixel centre."""
+    W, H, f = 1601, 41, 1200.0
+    cam = axis_camera(W, H, f)
+    cfg = oracle_cfg()
+    eps = cfg["flag_eps"]
+    k = 1400  # the pixel column past the box
+    Z, s = 4.0, np.log(0.01)
+
+    def splat(X):
+        return make_splats([[X, 0.0, Z]], [s, s, -12.0], 2.0, 0.8)
+
+    X = (k - 0.5 * W) * Z / f
+    for _ in range(6):  # Newton steps on the box edge u + ex - 1/2 = k - 1e-4
+        pre = O.preprocess(splat(X), cam, cfg)
+        u, S00, qc = pre["uvz"][0, 0], pre["cov2d"][0, 0], pre["qcut"][0]
+        ex = np.sqrt(S00 * qc * (1 + eps))
+        X += ((k - 1e-4) - (u + ex - 0.5)) * Z / f
+    pre = O.preprocess(splat(X), cam, cfg)
+    u, S00, qc = pre["uvz"][0, 0], pre["cov2d"][0, 0], pre["qcut"][0]
+    edge = u + np.sqrt(S00 * qc * (1 + eps)) - 0.5
+    assert k - 2e-4 < edge < k, edge  # pixel k is outside the box by about 1e-4 px
+    assert abs(pre["uvz"][0, 1] - (H // 2 + 0.5)) < 1e-12  # on the centre row's sample points
+    ref = O.render(splat(X), cam, cfg)
+    assert ref["flags"].reshape(H, W)[H // 2, k] & O.FLAG_SUPPORT  # the band reaches it
+    for cell in (1, 16):
+        got = O.render(splat(X), cam, dict(cfg, cell=cell))
+        np.testing.assert_array_equal(got["flags"], ref["flags"])
+    # sample points moved by a few 1e-4 px: the cell index still equals the brute-force loop
+    for shift in ((3e-4, 0.0), (0.0, -5e-4)):
+        ref = O.render(splat(X), cam, dict(cfg, shift=shift))
+        got = O.render(splat(X), cam, dict(cfg, shift=shift, cell=16))
+        for key in ref:
+            np.testing.assert_array_equal(got[key], ref[key], err_msg=key)
