@@ -66,6 +66,8 @@ def parse_args():
     p.add_argument("--tile", default=None, help="fix the tile shape, WxH (skips the autotuner)")
     p.add_argument("--batch", type=int, default=None, help="fix the prefetch distance (skips the autotuner)")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-persistent", action="store_true",
+                   help="render with one CTA per tile in tile order instead of the persistent longest-first queue")
     p.add_argument("--no-train-step", action="store_true", help="skip the step with the Eq. 8 loss")
     p.add_argument("--no-color16", action="store_true", help="skip the step with binary16 colour storage")
     p.add_argument("--no-gsr", action="store_true", help="skip the KNN build, the GSR point evaluation and the level-set extraction")
@@ -438,7 +440,7 @@ def main():
     inputs = api.scene_tensors(sc)
     P = sum(c.width * c.height for c in cams)
     ups = upstream_grads(P, 1000 + rank)
-    base = api.GESConfig(sh_degree=sc.sh_degree, persistent=1)
+    base = api.GESConfig(sh_degree=sc.sh_degree, persistent=0 if args.no_persistent else 1)
     if args.tile or args.batch:
         tw, th = (int(x) for x in (args.tile or f"{base.tile_w}x{base.tile_h}").split("x"))
         cfg = dataclasses.replace(base, tile_w=tw, tile_h=th, batch=args.batch or base.batch)
