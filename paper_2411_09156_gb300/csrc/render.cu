@@ -13,10 +13,10 @@
 // ahead of the chunk it evaluates into L2.
 //
 // The backward replays the list front to back from the stored t_final and
-// `last` (no per-pixel lists), and reduces each splat's 16 gradient values
-// across the warp with a transposing butterfly (16 shuffles for 16 values,
-// instead of 5 per value) before 16 lanes issue one coalesced set of FP32
-// atomics into the splat's 64-byte accumulator.
+// `last` (no per-pixel lists), and reduces each splat's gradient values (14, or
+// 10 without depth and normal) across the warp with a transposing butterfly
+// (15 or 12 shuffles in all, instead of 5 per value) before one lane of each
+// pair issues its value's FP32 atomic into the splat's 64-byte accumulator.
 #include "ges_internal.cuh"
 
 namespace ges {
@@ -197,43 +197,45 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
     }
 }
 
-// Warp sum of 16 values by recursive halving: after the five butterfly levels
-// lane L holds the full sum of value (L >> 1) & 15 (lanes L and L^1 agree).
-__device__ __forceinline__ float warp_reduce16(float (&g)[16], int lane) {
-    {
-        const bool up = lane & 16;
+// Warp sum of NV values by recursive halving. At the level with lane offset D a lane whose bit D
+// is clear keeps the first H = ceil(n / 2) of its n values and the other lane the rest (padded
+// with a zero when n is odd), each adding what its partner sends: NV - 1 + ... shuffles in all
+// (16 for 16 values, 12 for 10). After the levels 16, 8, 4, 2 each lane pair holds one value
+// index, reduce_label(NV, lane), or -1; the last level sums the pair.
+template <int D, int N>
+__device__ __forceinline__ void halve(float *g, int lane) {
+    constexpr int H = (N + 1) / 2;
+    const bool up = lane & D;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float send = up ? g[i] : g[i + 8];
-            const float keep = up ? g[i + 8] : g[i];
-            g[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-        }
+    for (int i = 0; i < H; ++i) {
+        const float rest = (H + i < N) ? g[H + i] : 0.f;
+        const float send = up ? g[i] : rest;
+        const float keep = up ? rest : g[i];
+        g[i] = keep + __shfl_xor_sync(0xffffffffu, send, D);
     }
-    {
-        const bool up = lane & 8;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float send = up ? g[i] : g[i + 4];
-            const float keep = up ? g[i + 4] : g[i];
-            g[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-        }
-    }
-    {
-        const bool up = lane & 4;
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const float send = up ? g[i] : g[i + 2];
-            const float keep = up ? g[i + 2] : g[i];
-            g[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-        }
-    }
-    {
-        const bool up = lane & 2;
-        const float send = up ? g[0] : g[1];
-        const float keep = up ? g[1] : g[0];
-        g[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    }
+}
+
+template <int NV>
+__device__ __forceinline__ float warp_reduce_n(float (&g)[NV], int lane) {
+    static_assert(NV >= 9 && NV <= 16, "four halvings leave one value");
+    constexpr int N1 = (NV + 1) / 2, N2 = (N1 + 1) / 2, N3 = (N2 + 1) / 2;
+    halve<16, NV>(g, lane);
+    halve<8, N1>(g, lane);
+    halve<4, N2>(g, lane);
+    halve<2, N3>(g, lane);
     return g[0] + __shfl_xor_sync(0xffffffffu, g[0], 1);
+}
+
+// The value index that lane's pair holds after warp_reduce_n<NV>, or -1 (a padding zero).
+__device__ __forceinline__ int reduce_label(int nv, int lane) {
+    int start = 0, valid = nv, n = nv;
+    for (int d = 16; d >= 2; d >>= 1) {
+        const int h = (n + 1) / 2;
+        if (lane & d) { start += h; valid = valid > h ? valid - h : 0; }
+        else valid = valid < h ? valid : h;
+        n = h;
+    }
+    return valid > 0 ? start : -1;
 }
 
 // FULL: the depth and normal outputs have upstream gradients too; without them (a loss on the
@@ -248,6 +250,13 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
     uint32_t *went = s_ent[warp];
     const uint32_t ahead = (uint32_t)a.batch;
     const float ln2 = 0.69314718055994531f;
+    // the gradient values a pair contributes, packed: 0-6 mean2d, Sigma', opacity, beta; then (FULL)
+    // depth; then colour; then (FULL) normal. This lane's pair adds value `lab` into slot `gslot` of
+    // the splat's 16-float accumulator (slot 11 and, without FULL, slots 7 and 12-15 stay 0).
+    constexpr int NV = FULL ? 14 : 10;
+    const int lab = reduce_label(NV, lane);
+    const int gslot = lab < 0 ? -1 : (FULL ? (lab < 11 ? lab : lab + 1) : (lab < 7 ? lab : lab + 1));
+    const bool writer = (lane & 1) == 0 && gslot >= 0;
     uint32_t tile;
     int sb;
     for (int it = 0; next_item(a.queue, a.counter, (uint32_t)a.V.n_tiles, NW, it, warp, lane, tile, sb); ++it) {
@@ -306,9 +315,9 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
             while (mask) {
                 const int bit = __ffs(mask) - 1;
                 mask &= mask - 1;
-                float g[16];
+                float g[NV];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) g[q] = 0.f;
+                for (int q = 0; q < NV; ++q) g[q] = 0.f;
                 bool contrib = false;
                 if (c0 + (uint32_t)bit < lp) {
                     const float4 r0 = slot[bit][0], r1 = slot[bit][1];
@@ -359,20 +368,21 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
                         g[2] = qx * mx;
                         g[3] = qx * my;
                         g[4] = qy * my;
-                        g[8] = gC0 * w;
-                        g[9] = gC1 * w;
-                        g[10] = gC2 * w;
+                        constexpr int c0i = FULL ? 8 : 7;  // first colour value
+                        g[c0i] = gC0 * w;
+                        g[c0i + 1] = gC1 * w;
+                        g[c0i + 2] = gC2 * w;
                         if (FULL) {
                             g[7] = gD * w;
-                            g[12] = gN0 * w;
-                            g[13] = gN1 * w;
-                            g[14] = gN2 * w;
+                            g[FULL ? 11 : 0] = gN0 * w;
+                            g[FULL ? 12 : 0] = gN1 * w;
+                            g[FULL ? 13 : 0] = gN2 * w;
                         }
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
-                    const float sum = warp_reduce16(g, lane);
-                    if ((lane & 1) == 0) atomicAdd(a.g2d + 16 * (size_t)went[bit] + (lane >> 1), sum);
+                    const float sum = warp_reduce_n<NV>(g, lane);
+                    if (writer) atomicAdd(a.g2d + 16 * (size_t)went[bit] + gslot, sum);
                 }
             }
             __syncwarp();
