@@ -77,7 +77,7 @@ extern "C" {
 #define GES_API
 #endif
 
-#define GES_ABI_VERSION 2
+#define GES_ABI_VERSION 3
 #define GES_MAX_VIEWS 32
 
 typedef enum ges_status {
@@ -87,7 +87,9 @@ typedef enum ges_status {
     GES_ERR_CUDA = 3,        /* a CUDA launch or copy failed */
     GES_ERR_NUMERIC = 4,     /* a splat had a non-finite position, opacity or beta, a beta <= 0, or (if
                                 visible) a non-finite projection; it was culled */
-    GES_ERR_TOO_LARGE = 5    /* the problem exceeds the fixed scratch of ges_render_bwd_noalloc */
+    GES_ERR_TOO_LARGE = 5,   /* the problem exceeds the fixed scratch of ges_render_bwd_noalloc */
+    GES_ERR_BOUNDS = 6       /* debug build only: a device-side bounds check failed; the access was
+                                skipped (see ges_build_flags) */
 } ges_status;
 
 /* Pinhole camera. viewmat: row-major 3x4 world-to-camera [R | t]; camera x right,
@@ -446,6 +448,14 @@ GES_API const char *ges_status_string(ges_status s);
  * launch with events on `stream`. */
 GES_API ges_status ges_peak_run(int32_t kind, int32_t blocks_per_sm, int32_t iters, float *sink,
                                 uint64_t sink_floats, void *stream, uint64_t *ops);
+
+/* Build flags of the loaded library: bit 0 set in the debug build (compiled with GES_DEBUG),
+ * whose render kernels check every list entry they read against the number of (view, splat)
+ * entries, and every pixel's replay end against its tile's list, before they use it: a failed
+ * check records GES_ERR_BOUNDS in the error word (ges_sync_status) and skips the access instead
+ * of faulting. The release build has no such checks. */
+#define GES_BUILD_DEBUG 1
+GES_API int32_t ges_build_flags(void);
 
 /* GES_ABI_VERSION of the loaded library. */
 GES_API int32_t ges_abi_version(void);

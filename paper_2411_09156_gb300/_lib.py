@@ -13,8 +13,10 @@ from . import build as _build
 
 MAX_VIEWS = 32
 STATUS_NAMES = {0: "GES_OK", 1: "GES_ERR_INVALID_ARG", 2: "GES_ERR_CAPACITY", 3: "GES_ERR_CUDA",
-                4: "GES_ERR_NUMERIC", 5: "GES_ERR_TOO_LARGE"}
-GES_OK, GES_ERR_INVALID_ARG, GES_ERR_CAPACITY, GES_ERR_CUDA, GES_ERR_NUMERIC, GES_ERR_TOO_LARGE = range(6)
+                4: "GES_ERR_NUMERIC", 5: "GES_ERR_TOO_LARGE", 6: "GES_ERR_BOUNDS"}
+GES_OK, GES_ERR_INVALID_ARG, GES_ERR_CAPACITY, GES_ERR_CUDA, GES_ERR_NUMERIC, GES_ERR_TOO_LARGE, GES_ERR_BOUNDS = \
+    range(7)
+GES_BUILD_DEBUG = 1
 NOALLOC_MAX_ENTRIES = 524288
 
 
@@ -54,6 +56,7 @@ _CAM = ctypes.POINTER(Camera)
 _CFG = ctypes.POINTER(Config)
 SIGNATURES = {
     "ges_abi_version": (ctypes.c_int32, []),
+    "ges_build_flags": (ctypes.c_int32, []),
     "ges_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ges_proj_bytes": (_S, [_I, _I]),
     "ges_bins_bytes": (_S, [_I, _I, _CAM, _CFG, ctypes.c_uint64]),
@@ -92,8 +95,14 @@ _lock = threading.Lock()
 _lib = None
 
 
+def debug_variant() -> bool:
+    """GES_LIB_VARIANT=debug in the environment selects the debug build (device-side bounds
+    checks, see ges_build_flags) for this process."""
+    return os.environ.get("GES_LIB_VARIANT", "") == "debug"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.lib_path(debug_variant())
 
 
 def lib(build_if_missing: bool = True) -> ctypes.CDLL:
@@ -101,7 +110,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build() if build_if_missing else _build.LIB
+            dbg = debug_variant()
+            path = _build.build(debug=dbg) if build_if_missing else _build.lib_path(dbg)
             if not os.path.exists(path):
                 raise RuntimeError(f"libges.so not found at {path}; the GES rasterizer has no CPU fallback")
             L = ctypes.CDLL(path)

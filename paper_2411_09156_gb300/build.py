@@ -31,7 +31,12 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the GES CUDA library cannot be built")
 
 
-def _stamp() -> str:
+def lib_path(debug: bool = False) -> str:
+    """The release library, or the debug build (GES_DEBUG: device-side bounds checks) beside it."""
+    return os.path.join(BUILD, "debug", "libges.so") if debug else LIB
+
+
+def _stamp(flags) -> str:
     h = hashlib.sha256()
     for f in sorted(os.listdir(CSRC)) + ["../../include/ges.h"]:
         p = os.path.normpath(os.path.join(CSRC, f))
@@ -39,24 +44,29 @@ def _stamp() -> str:
             h.update(f.encode())
             with open(p, "rb") as fh:
                 h.update(fh.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(" ".join(ARCH + flags).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    stamp_path = os.path.join(BUILD, "libges.stamp")
-    stamp = _stamp()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_path):
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compiles and links the library (or its debug build) unless the sources and flags are
+    unchanged since the last build; returns its path."""
+    out_dir = os.path.join(BUILD, "debug") if debug else BUILD
+    lib = lib_path(debug)
+    flags = FLAGS + (["-DGES_DEBUG"] if debug else [])
+    os.makedirs(out_dir, exist_ok=True)
+    stamp_path = os.path.join(out_dir, "libges.stamp")
+    stamp = _stamp(flags)
+    if not force and os.path.exists(lib) and os.path.exists(stamp_path):
         with open(stamp_path) as fh:
             if fh.read().strip() == stamp:
-                return LIB
+                return lib
     nvcc = _nvcc()
     # -fvisibility=hidden: only the GES_API functions of include/ges.h are exported
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc] + ARCH + FLAGS + ["-I" + INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
+        cmd = [nvcc] + ARCH + flags + ["-I" + INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -66,15 +76,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp_path, "w") as fh:
         fh.write(stamp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

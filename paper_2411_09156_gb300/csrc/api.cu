@@ -123,6 +123,14 @@ extern "C" {
 
 int32_t ges_abi_version(void) { return GES_ABI_VERSION; }
 
+int32_t ges_build_flags(void) {
+#ifdef GES_DEBUG
+    return GES_BUILD_DEBUG;
+#else
+    return 0;
+#endif
+}
+
 const char *ges_status_string(ges_status s) {
     switch (s) {
         case GES_OK: return "ok";
@@ -131,6 +139,7 @@ const char *ges_status_string(ges_status s) {
         case GES_ERR_CUDA: return "CUDA error";
         case GES_ERR_NUMERIC: return "non-finite input or projection; splat culled";
         case GES_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of the no-allocation entry point";
+        case GES_ERR_BOUNDS: return "device-side bounds check failed (debug build); access skipped";
         default: return "unknown status";
     }
 }
@@ -150,6 +159,7 @@ size_t ges_bins_bytes(int32_t n, int32_t n_views, const ges_camera *cams, const 
 
 ges_status ges_get_layout(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
                           uint64_t capacity, ges_layout *out) {
+    GES_RANGE();
     if (!out || !check_views(n, n_views, cams, cfg) || capacity > 0xfffffffeull) return GES_ERR_INVALID_ARG;
     const ViewSet V = make_views(n_views, cams, cfg);
     const ProjLayout P = proj_layout(n, n_views);
@@ -204,6 +214,7 @@ static ges_status preprocess_impl(int32_t n, int32_t first, int32_t count, const
 ges_status ges_preprocess(int32_t n, const float *pos_op, const float *lscale_beta, const float *quat,
                           const void *color, int32_t n_views, const ges_camera *cams, const ges_config *cfg,
                           void *proj, size_t proj_bytes, void *stream) {
+    GES_RANGE();
     return preprocess_impl(n, 0, n, pos_op, lscale_beta, quat, color, n_views, cams, cfg, proj, proj_bytes, stream);
 }
 
@@ -211,11 +222,13 @@ ges_status ges_preprocess_range(int32_t n, int32_t first, int32_t count, const f
                                 const float *lscale_beta, const float *quat, const void *color, int32_t n_views,
                                 const ges_camera *cams, const ges_config *cfg, void *proj, size_t proj_bytes,
                                 void *stream) {
+    GES_RANGE();
     return preprocess_impl(n, first, count, pos_op, lscale_beta, quat, color, n_views, cams, cfg, proj, proj_bytes,
                            stream);
 }
 
 ges_status ges_instance_count(const void *proj, size_t proj_bytes, uint64_t *count, void *stream) {
+    GES_RANGE();
     if (!proj || !count || proj_bytes < 256) return GES_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned long long v = 0;
@@ -227,6 +240,7 @@ ges_status ges_instance_count(const void *proj, size_t proj_bytes, uint64_t *cou
 
 ges_status ges_bin(int32_t n, int32_t n_views, const ges_camera *cams, const ges_config *cfg, void *proj,
                    size_t proj_bytes, void *bins, size_t bins_bytes, void *stream) {
+    GES_RANGE();
     if (!check_views(n, n_views, cams, cfg) || !proj || !bins || !aligned16(proj) || !aligned16(bins))
         return GES_ERR_INVALID_ARG;
     const ProjLayout PL = proj_layout(n, n_views);
@@ -270,6 +284,7 @@ ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *cams, co
                           const void *proj, size_t proj_bytes, const void *bins, size_t bins_bytes, float *color,
                           float *depth, float *alpha, float *normal, float *t_final, uint32_t *last,
                           uint32_t *n_contrib, uint32_t *n_eval, void *stream) {
+    GES_RANGE();
     if (!check_views(n, n_views, cams, cfg) || !proj || !bins || !color || !alpha || !t_final || !last || !n_contrib)
         return GES_ERR_INVALID_ARG;
     const ProjLayout PL = proj_layout(n, n_views);
@@ -289,6 +304,8 @@ ges_status ges_render_fwd(int32_t n, int32_t n_views, const ges_camera *cams, co
     a.color = color; a.depth = depth; a.alpha = alpha; a.normal = normal; a.t_final = t_final;
     a.last = last; a.n_contrib = n_contrib; a.n_eval = n_eval;
     a.n_events = n_eval ? const_cast<unsigned long long *>(at<unsigned long long>(bins, 16)) : nullptr;
+    a.n_entries = (uint32_t)((uint64_t)n * n_views);
+    a.err = const_cast<uint32_t *>(at<uint32_t>(proj, 8));
     a.batch = cfg->batch;
     a.alpha_min = cfg->alpha_min; a.alpha_max = cfg->alpha_max; a.t_min = cfg->t_min;
     for (int c = 0; c < 3; ++c) a.bg[c] = cfg->bg[c];
@@ -303,6 +320,7 @@ ges_status ges_render_bwd_screen(int32_t n, int32_t n_views, const ges_camera *c
                                  const float *color, const float *depth, const float *normal, const float *t_final,
                                  const uint32_t *last, const float *g_color, const float *g_depth,
                                  const float *g_alpha, const float *g_normal, float *g2d, void *stream) {
+    GES_RANGE();
     if (!check_views(n, n_views, cams, cfg) || !proj || !bins || !t_final || !last) return GES_ERR_INVALID_ARG;
     if ((g_color && !color) || (g_depth && !depth) || (g_normal && !normal)) return GES_ERR_INVALID_ARG;
     if (g2d && !aligned16(g2d)) return GES_ERR_INVALID_ARG;
@@ -326,6 +344,8 @@ ges_status ges_render_bwd_screen(int32_t n, int32_t n_views, const ges_camera *c
     b.color = color; b.depth = depth; b.normal = normal; b.t_final = t_final; b.last = last;
     b.g_color = g_color; b.g_depth = g_depth; b.g_alpha = g_alpha; b.g_normal = g_normal;
     b.g2d = acc;
+    b.n_entries = (uint32_t)((uint64_t)n * n_views);
+    b.err = at<uint32_t>(proj, 8);
     b.batch = cfg->batch;
     b.alpha_min = cfg->alpha_min; b.alpha_max = cfg->alpha_max;
     b.V = V;
@@ -372,6 +392,7 @@ ges_status ges_preprocess_bwd(int32_t n, int32_t n_views, const ges_camera *cams
                               const float *pos_op, const float *lscale_beta, const float *quat, const void *color_in,
                               const void *proj, size_t proj_bytes, const float *g2d, float *g_pos_op,
                               float *g_lscale_beta, float *g_quat, float *g_color_in, void *stream) {
+    GES_RANGE();
     return preprocess_bwd_impl(n, 0, n, n_views, cams, cfg, pos_op, lscale_beta, quat, color_in, proj, proj_bytes,
                                g2d, g_pos_op, g_lscale_beta, g_quat, g_color_in, stream);
 }
@@ -381,6 +402,7 @@ ges_status ges_preprocess_bwd_range(int32_t n, int32_t first, int32_t count, int
                                     const float *lscale_beta, const float *quat, const void *color_in,
                                     const void *proj, size_t proj_bytes, const float *g2d, float *g_pos_op,
                                     float *g_lscale_beta, float *g_quat, float *g_color_in, void *stream) {
+    GES_RANGE();
     return preprocess_bwd_impl(n, first, count, n_views, cams, cfg, pos_op, lscale_beta, quat, color_in, proj,
                                proj_bytes, g2d, g_pos_op, g_lscale_beta, g_quat, g_color_in, stream);
 }
@@ -392,6 +414,7 @@ ges_status ges_render_bwd(int32_t n, int32_t n_views, const ges_camera *cams, co
                           const float *g_color, const float *g_depth, const float *g_alpha, const float *g_normal,
                           float *g_pos_op, float *g_lscale_beta, float *g_quat, float *g_color_in, float *g2d,
                           void *stream) {
+    GES_RANGE();
     // check both halves' arguments before launching either
     if (n > 0 && (!pos_op || !lscale_beta || !quat || !color_in || !g_pos_op || !g_lscale_beta || !g_quat ||
                   !g_color_in || !aligned16(pos_op) || !aligned16(lscale_beta) || !aligned16(quat) ||
@@ -405,6 +428,7 @@ ges_status ges_render_bwd(int32_t n, int32_t n_views, const ges_camera *cams, co
 }
 
 ges_status ges_sync_status(void *proj, size_t proj_bytes, void *stream) {
+    GES_RANGE();
     if (!proj || proj_bytes < 256) return GES_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint32_t word = 0;
@@ -413,6 +437,7 @@ ges_status ges_sync_status(void *proj, size_t proj_bytes, void *stream) {
         return GES_ERR_CUDA;
     if (cudaMemsetAsync(static_cast<char *>(proj) + 8, 0, 4, s) != cudaSuccess) return GES_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return GES_ERR_CUDA;
+    if (word & kErrBounds) return GES_ERR_BOUNDS;
     if (word & kErrCapacity) return GES_ERR_CAPACITY;
     if (word & kErrNumeric) return GES_ERR_NUMERIC;
     return GES_OK;

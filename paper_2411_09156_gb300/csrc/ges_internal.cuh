@@ -5,11 +5,22 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "ges.h"
 
 namespace ges {
+
+// NVTX range named after the C-ABI entry point, for timelines of profiling tools (a no-op
+// when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define GES_RANGE() ::ges::NvtxRange ges_range_(__func__)
 
 constexpr int kMaxViews = GES_MAX_VIEWS;
 constexpr uint32_t kCulledKey = 0xffffffffu;
@@ -21,6 +32,7 @@ constexpr float kNegHalfLog2e = -0.72134752044448170f;
 // Error-word bits (1 << ges_status).
 constexpr uint32_t kErrCapacity = 1u << GES_ERR_CAPACITY;
 constexpr uint32_t kErrNumeric = 1u << GES_ERR_NUMERIC;
+constexpr uint32_t kErrBounds = 1u << GES_ERR_BOUNDS;
 
 // Per-view constants handed to every kernel by value.
 struct ViewSet {
@@ -411,6 +423,8 @@ struct FwdArgs {
     float *color, *depth, *alpha, *normal, *t_final;
     uint32_t *last, *n_contrib, *n_eval;
     unsigned long long *n_events;  // with n_eval: (warp block, splat) pairs passing the warp cull
+    uint32_t n_entries;            // (view, splat) entries: the bound of every listed entry
+    uint32_t *err;                 // error word (debug-build bounds checks)
     int batch;
     float alpha_min, alpha_max, t_min;
     float bg[3];
@@ -427,6 +441,8 @@ struct BwdArgs {
     const uint32_t *last;
     const float *g_color, *g_depth, *g_alpha, *g_normal;
     float *g2d;
+    uint32_t n_entries;  // (view, splat) entries: the bound of every listed entry
+    uint32_t *err;       // error word (debug-build bounds checks)
     int batch;
     float alpha_min, alpha_max;
     ViewSet V;

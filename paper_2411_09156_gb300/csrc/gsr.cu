@@ -369,6 +369,7 @@ extern "C" ges_status ges_gsr(int32_t n, const float *pos_op, const float *lscal
                               const float *sample_z, float lambda_sdf, float lambda_nor, void *workspace,
                               size_t workspace_bytes, float *losses, float *sample_out, float *g_pos_op,
                               float *g_lscale_beta, float *g_quat, void *stream) {
+    GES_RANGE();
     if (n < 1 || m < 1 || (uint64_t)n > (1ull << 26) || (uint64_t)m > (1ull << 28)) return GES_ERR_INVALID_ARG;
     if (!pos_op || !lscale_beta || !quat || !cfg || !knn || !sample_splat || !sample_z || !workspace || !losses)
         return GES_ERR_INVALID_ARG;

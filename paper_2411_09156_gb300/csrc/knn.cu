@@ -504,6 +504,7 @@ cudaError_t knn_points_run(int32_t n, const float4 *pos, int32_t m, const float4
 
 extern "C" ges_status ges_knn(int32_t n, const float *pos_op, void *workspace, size_t workspace_bytes, int32_t *knn,
                               void *stream) {
+    GES_RANGE();
     if (n < GES_KNN_K || (uint64_t)n > (1ull << 26) || !pos_op || !workspace || !knn) return GES_ERR_INVALID_ARG;
     if (((uintptr_t)pos_op & 15u) || ((uintptr_t)workspace & 255u) || ((uintptr_t)knn & 3u))
         return GES_ERR_INVALID_ARG;
@@ -524,6 +525,7 @@ extern "C" size_t ges_knn_points_workspace_bytes(int32_t n, int32_t m) {
 
 extern "C" ges_status ges_knn_points(int32_t n, const float *pos_op, int32_t m, const float *points,
                                      void *workspace, size_t workspace_bytes, int32_t *knn, void *stream) {
+    GES_RANGE();
     if (n < GES_KNN_K || (uint64_t)n > (1ull << 26) || m < 1 || (uint64_t)m > (1ull << 28)) return GES_ERR_INVALID_ARG;
     if (!pos_op || !points || !workspace || !knn) return GES_ERR_INVALID_ARG;
     if (((uintptr_t)pos_op & 15u) || ((uintptr_t)points & 15u) || ((uintptr_t)workspace & 255u) ||

@@ -261,6 +261,7 @@ extern "C" ges_status ges_levelset(int32_t n, const float *pos_op, const float *
                                    const ges_config *cfg, int32_t n_views, const ges_camera *cams, const float *depth,
                                    const float *alpha, int32_t m, const int32_t *pixels, int32_t n_steps, float level,
                                    void *workspace, size_t workspace_bytes, float *points, void *stream) {
+    GES_RANGE();
     if (n < GES_KNN_K || (uint64_t)n > (1ull << 26) || m < 1 || (uint64_t)m > (1ull << 28)) return GES_ERR_INVALID_ARG;
     if (!pos_op || !lscale_beta || !quat || !cfg || !cams || !depth || !alpha || !pixels || !workspace || !points)
         return GES_ERR_INVALID_ARG;

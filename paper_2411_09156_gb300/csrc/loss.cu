@@ -292,6 +292,7 @@ extern "C" size_t ges_loss_workspace_bytes(int32_t n_views, const ges_camera *ca
 extern "C" ges_status ges_loss_rgb(int32_t n_views, const ges_camera *cams, const float *color, const float *target,
                                    float lambda, void *workspace, size_t workspace_bytes, float *loss, float *g_color,
                                    void *stream) {
+    GES_RANGE();
     if (!loss_views_ok(n_views, cams) || !color || !target || !workspace || !loss) return GES_ERR_INVALID_ARG;
     if (!(lambda >= 0.f && lambda <= 1.f)) return GES_ERR_INVALID_ARG;
     if (((uintptr_t)workspace & 7u) != 0) return GES_ERR_INVALID_ARG;

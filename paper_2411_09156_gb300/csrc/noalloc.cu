@@ -54,6 +54,7 @@ extern "C" ges_status ges_render_bwd_noalloc(
     const void *bins, size_t bins_bytes, const float *color, const float *depth, const float *normal,
     const float *t_final, const uint32_t *last, const float *g_color, const float *g_depth, const float *g_alpha,
     const float *g_normal, float *g_pos_op, float *g_lscale_beta, float *g_quat, float *g_color_in, void *stream) {
+    GES_RANGE();
     if (n < 0 || n_views < 1) return GES_ERR_INVALID_ARG;
     if ((uint64_t)n * (uint64_t)n_views > kMaxEntries) return GES_ERR_TOO_LARGE;
     float *acc = nullptr;

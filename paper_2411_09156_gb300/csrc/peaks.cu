@@ -70,6 +70,7 @@ using namespace ges;
 
 ges_status ges_peak_run(int32_t kind, int32_t blocks_per_sm, int32_t iters, float *sink, uint64_t sink_floats,
                         void *stream, uint64_t *ops) {
+    GES_RANGE();
     if (kind < 0 || kind > 3 || blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || !sink || !ops)
         return GES_ERR_INVALID_ARG;
     if (sink_floats < (uint64_t)kPeakThreads) return GES_ERR_INVALID_ARG;

@@ -89,11 +89,24 @@ __device__ __forceinline__ bool warp_may_hit(float u, float v, float a, float b,
     return best <= qm;
 }
 
+// Debug build: an entry read from a tile list must name one of the n_entries (view, splat)
+// records; if it does not, the error word records GES_ERR_BOUNDS and the entry is skipped.
+__device__ __forceinline__ bool entry_ok(uint32_t e, uint32_t n_entries, uint32_t *err) {
+#ifdef GES_DEBUG
+    if (e >= n_entries) {
+        set_error(err, kErrBounds);
+        return false;
+    }
+#endif
+    return true;
+}
+
 // Loads record e, tests it against the warp's block and, if it can contribute,
 // stores it (with 2b in place of b) into the warp's slot `lane`.
-__device__ __forceinline__ bool load_cull_stage(const float4 *rec, uint32_t e, float rx0, float rx1, float ry0,
-                                                float ry1, float4 (*slot)[4], int lane) {
-    if (e == kNone) return false;
+__device__ __forceinline__ bool load_cull_stage(const float4 *rec, uint32_t e, uint32_t n_entries, uint32_t *err,
+                                                float rx0, float rx1, float ry0, float ry1, float4 (*slot)[4],
+                                                int lane) {
+    if (e == kNone || !entry_ok(e, n_entries, err)) return false;
     const float4 *r = rec + 4 * (size_t)e;
     float4 r0 = __ldg(r);
     const float4 r1 = __ldg(r + 1);
@@ -138,10 +151,10 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
         uint32_t e_pf = entry_or_none(a.inst_entry, rg.x + ahead + lane, rg.y);
         for (uint32_t c0 = rg.x; c0 < rg.y; c0 += 32) {
             if (__all_sync(0xffffffffu, done)) break;
-            if (e_pf != kNone) prefetch_l2(a.rec + 4 * (size_t)e_pf);
+            if (e_pf != kNone && entry_ok(e_pf, a.n_entries, a.err)) prefetch_l2(a.rec + 4 * (size_t)e_pf);
             e_pf = entry_or_none(a.inst_entry, c0 + 32 + ahead + lane, rg.y);
             const uint32_t e_nxt = entry_or_none(a.inst_entry, c0 + 32 + lane, rg.y);
-            const bool hit = load_cull_stage(a.rec, e_cur, rx0, rx1, ry0, ry1, slot, lane);
+            const bool hit = load_cull_stage(a.rec, e_cur, a.n_entries, a.err, rx0, rx1, ry0, ry1, slot, lane);
             e_cur = e_nxt;
             uint32_t mask = __ballot_sync(0xffffffffu, hit);
             events += __popc(mask);
@@ -284,6 +297,12 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
             const long long g = a.V.pix_base[v] + pix;
             const long long c3 = 3 * a.V.pix_base[v] + pix;
             lp = a.last[g];
+#ifdef GES_DEBUG
+            if (lp < rg.x || lp > rg.y) {  // the replay stays inside this tile's list
+                set_error(a.err, kErrBounds);
+                lp = rg.x;
+            }
+#endif
             if (a.g_color) {
                 gC0 = a.g_color[c3]; gC1 = a.g_color[c3 + P]; gC2 = a.g_color[c3 + 2 * P];
                 Cf0 = a.color[c3]; Cf1 = a.color[c3 + P]; Cf2 = a.color[c3 + 2 * P];
@@ -304,10 +323,10 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
         uint32_t e_cur = entry_or_none(a.inst_entry, rg.x + lane, wend);
         uint32_t e_pf = entry_or_none(a.inst_entry, rg.x + ahead + lane, wend);
         for (uint32_t c0 = rg.x; c0 < wend; c0 += 32) {
-            if (e_pf != kNone) prefetch_l2(a.rec + 4 * (size_t)e_pf);
+            if (e_pf != kNone && entry_ok(e_pf, a.n_entries, a.err)) prefetch_l2(a.rec + 4 * (size_t)e_pf);
             e_pf = entry_or_none(a.inst_entry, c0 + 32 + ahead + lane, wend);
             const uint32_t e_nxt = entry_or_none(a.inst_entry, c0 + 32 + lane, wend);
-            const bool hit = load_cull_stage(a.rec, e_cur, rx0, rx1, ry0, ry1, slot, lane);
+            const bool hit = load_cull_stage(a.rec, e_cur, a.n_entries, a.err, rx0, rx1, ry0, ry1, slot, lane);
             if (hit) went[lane] = e_cur;
             e_cur = e_nxt;
             uint32_t mask = __ballot_sync(0xffffffffu, hit);

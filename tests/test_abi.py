@@ -30,7 +30,8 @@ def test_library_exports_every_declared_function():
         assert hasattr(lib, name), name
         assert name in _lib.SIGNATURES, f"binding lacks {name}"
     assert set(_lib.SIGNATURES) == set(names)
-    assert lib.ges_abi_version() == 2
+    assert lib.ges_abi_version() == 3
+    assert lib.ges_build_flags() == 0  # the release build (no device-side bounds checks)
 
 
 def test_built_for_sm103a_only():
