@@ -88,6 +88,7 @@ typedef struct {
     double normal[3];
     double facing; /* n . (campos - mu) / |campos - mu| before the sign flip */
     double du, dv; /* bound on the float32 rounding of (u, v) on the GPU side (pixels), for the flags */
+    double qflag;  /* Q beyond which the splat neither passes the support test nor sets a flag */
 } orc_splat;
 
 /* ------------------------------------------------------------------ helpers */
@@ -184,6 +185,20 @@ static float depth32(const float vm[12], const double mu[3]) {
     volatile float s2 = s + c;
     volatile float r = s2 + vm[11];
     return r;
+}
+
+/* Squared Mahalanobis radius beyond which a splat changes no pixel's loop: it passes the support
+ * test only where Q <= qcut, and sets the support-edge flag only where Q <= q* + dQ with
+ * q* = qcut (1 + flag_eps) and dQ as in render_pixel. With r = sqrt(Q), |C d| <= sqrt(lam) r (lam
+ * the largest eigenvalue of the conic C) and dQ <= 2 sqrt2 delta |C d| + 2^-20 Q (delta =
+ * max(du, dv)), both need (1 - 2^-20) r^2 - 2 sqrt2 delta sqrt(lam) r - q* <= 0, i.e. r <= r_max;
+ * returns r_max^2 (1 + 1e-9). */
+static double flag_radius2(const orc_splat *s, double eps) {
+    const double c0 = s->conic[0], c1 = s->conic[1], c2 = s->conic[2];
+    const double lam = 0.5 * (c0 + c2) + sqrt(0.25 * (c0 - c2) * (c0 - c2) + c1 * c1);
+    const double dl = s->du > s->dv ? s->du : s->dv, k = 1.0 - ldexp(1.0, -20);
+    const double rmax = (sqrt(2.0 * lam) * dl + sqrt(2.0 * lam * dl * dl + k * s->qcut * (1.0 + eps))) / k;
+    return rmax * rmax * (1.0 + 1e-9);
 }
 
 /* ------------------------------------------------------------ S1 - S4 */
@@ -293,6 +308,7 @@ static void project_splat(const double *pos_op, const double *lsb, const double 
     s->facing = f;
     double sg = (f < 0) ? -1.0 : 1.0;
     for (int j = 0; j < 3; ++j) s->normal[j] = sg * n[j];
+    s->qflag = flag_radius2(s, cfg->flag_eps);
     s->visible = 1;
 }
 
@@ -325,15 +341,10 @@ static int32_t *visible_order(int n, const orc_splat *sp, int *n_vis) {
 /* ------------------------------------------------------------ cell index
  * The image is cut into cells of c x c pixels. Each cell lists, in the depth
  * order of S5, every visible splat whose widened support box reaches a pixel
- * centre of the cell. A splat changes a pixel's loop only where it passes the
- * support test (Q <= qcut) or sets the support-edge flag, Q <= q* + dQ with
- * q* = qcut (1 + flag_eps) and dQ as in render_pixel. With r = sqrt(Q), |C d| <=
- * sqrt(lam) r (lam the largest eigenvalue of the conic C) and
- * dQ <= 2 sqrt2 delta |C d| + 2^-20 Q (delta = max(du, dv)), both need
- * r (1 - 2^-20) r - 2 sqrt2 delta sqrt(lam) r - q* <= 0, i.e. r <= r_max. The box
- * of the ellipse Q <= q (Q = d^T Sigma'^-1 d) is |dx| <= sqrt(q Sigma'_00),
- * |dy| <= sqrt(q Sigma'_11), taken at q = r_max^2 (1 + 1e-9) and widened by
- * 1e-6 px. A splat that a pixel's cell does not list is therefore a no-op step
+ * centre of the cell. A splat changes a pixel's loop only where Q <= qflag
+ * (flag_radius2). The box of the ellipse Q <= q (Q = d^T Sigma'^-1 d) is
+ * |dx| <= sqrt(q Sigma'_00), |dy| <= sqrt(q Sigma'_11), taken at q = qflag and
+ * widened by 1e-6 px. A splat that a pixel's cell does not list is therefore a no-op step
  * of that pixel's loop, and the loop over the cell's list gives the result of
  * the loop over all splats bit for bit. */
 typedef struct {
@@ -344,11 +355,8 @@ typedef struct {
 
 static int cell_box(const orc_splat *s, const orc_camera *cam, double eps, const float shift[2], int c, int *cx0,
                     int *cx1, int *cy0, int *cy1) {
-    const double c0 = s->conic[0], c1 = s->conic[1], c2 = s->conic[2];
-    const double lam = 0.5 * (c0 + c2) + sqrt(0.25 * (c0 - c2) * (c0 - c2) + c1 * c1);
-    const double dl = s->du > s->dv ? s->du : s->dv, k = 1.0 - ldexp(1.0, -20);
-    const double rmax = (sqrt(2.0 * lam) * dl + sqrt(2.0 * lam * dl * dl + k * s->qcut * (1.0 + eps))) / k;
-    const double q = rmax * rmax * (1.0 + 1e-9);
+    (void)eps;
+    const double q = s->qflag;
     const double ex = sqrt(s->S[0] * q) + 1e-6 + fabs(shift[0]), ey = sqrt(s->S[2] * q) + 1e-6 + fabs(shift[1]);
     /* pixel x (sampled at x + 0.5 + shift, |shift| added to ex above) can be in the support iff
        |x + 0.5 - u| <= ex */
@@ -430,6 +438,7 @@ static void render_pixel(const int32_t *ord, int nv, const orc_splat *sp, double
         const orc_splat *s = &sp[ord[k]];
         double dx = px - s->u, dy = py - s->v;
         double Q = s->conic[0] * dx * dx + 2.0 * s->conic[1] * dx * dy + s->conic[2] * dy * dy;
+        if (Q > s->qflag) continue; /* outside the support and every band: a no-op step */
         const double mx = s->conic[0] * dx + s->conic[1] * dy, my = s->conic[1] * dx + s->conic[2] * dy;
         const double dQ = 2.0 * (fabs(mx) * s->du + fabs(my) * s->dv) + ldexp(fabs(Q), -20);
         if (fabs(Q - s->qcut) <= eps * s->qcut + dQ) flags |= FLAG_SUPPORT;
