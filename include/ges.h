@@ -105,7 +105,7 @@ typedef struct ges_camera {
  * tile 16x16, batch 256, phi_mode 1, rho 0.1, lowpass 0.3, alpha_min 1/255,
  * alpha_max 0.99, t_min 1e-4, jac_clamp 1.3. */
 typedef struct ges_config {
-    int32_t tile_w, tile_h; /* 16x16, 8x8, 32x8 or 8x32 */
+    int32_t tile_w, tile_h; /* 16x16, 16x8, 8x16, 8x8, 32x8 or 8x32 */
     int32_t batch;          /* render: list entries each warp prefetches ahead of the 32 it evaluates
                                (32..256, multiple of 32) */
     int32_t sh_degree;      /* -1 (RGB given) or 0..3 */

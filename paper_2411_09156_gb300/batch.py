@@ -206,7 +206,7 @@ class BatchPlan:
 
 
 # --------------------------------------------------------------------------- autotune
-TILE_SHAPES = ((16, 16), (8, 8), (32, 8), (8, 32))
+TILE_SHAPES = ((16, 16), (16, 8), (8, 16), (8, 8), (32, 8), (8, 32))
 BATCHES = (128, 256)
 AUTOTUNE_FILE = os.path.join(_build.BUILD, "autotune.json")
 

@@ -440,7 +440,8 @@ static cudaError_t launch_bwd_t(const BwdArgs &a, cudaStream_t s) {
 }
 
 bool tile_shape_supported(int tw, int th) {
-    return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8) || (tw == 8 && th == 32);
+    return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8) || (tw == 8 && th == 32) ||
+           (tw == 16 && th == 8) || (tw == 8 && th == 16);
 }
 
 cudaError_t launch_render_fwd(const FwdArgs &a, cudaStream_t s) {
@@ -449,6 +450,8 @@ cudaError_t launch_render_fwd(const FwdArgs &a, cudaStream_t s) {
     if (tw == 16 && th == 16) return dn ? launch_fwd_t<16, 16, true>(a, s) : launch_fwd_t<16, 16, false>(a, s);
     if (tw == 8 && th == 8) return dn ? launch_fwd_t<8, 8, true>(a, s) : launch_fwd_t<8, 8, false>(a, s);
     if (tw == 8 && th == 32) return dn ? launch_fwd_t<8, 32, true>(a, s) : launch_fwd_t<8, 32, false>(a, s);
+    if (tw == 16 && th == 8) return dn ? launch_fwd_t<16, 8, true>(a, s) : launch_fwd_t<16, 8, false>(a, s);
+    if (tw == 8 && th == 16) return dn ? launch_fwd_t<8, 16, true>(a, s) : launch_fwd_t<8, 16, false>(a, s);
     return dn ? launch_fwd_t<32, 8, true>(a, s) : launch_fwd_t<32, 8, false>(a, s);
 }
 
@@ -458,6 +461,8 @@ cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s) {
     if (tw == 16 && th == 16) return full ? launch_bwd_t<16, 16, true>(a, s) : launch_bwd_t<16, 16, false>(a, s);
     if (tw == 8 && th == 8) return full ? launch_bwd_t<8, 8, true>(a, s) : launch_bwd_t<8, 8, false>(a, s);
     if (tw == 8 && th == 32) return full ? launch_bwd_t<8, 32, true>(a, s) : launch_bwd_t<8, 32, false>(a, s);
+    if (tw == 16 && th == 8) return full ? launch_bwd_t<16, 8, true>(a, s) : launch_bwd_t<16, 8, false>(a, s);
+    if (tw == 8 && th == 16) return full ? launch_bwd_t<8, 16, true>(a, s) : launch_bwd_t<8, 16, false>(a, s);
     return full ? launch_bwd_t<32, 8, true>(a, s) : launch_bwd_t<32, 8, false>(a, s);
 }
 

@@ -100,7 +100,7 @@ def _check_binning(sc, cams, tile):
     return np.where(vis, (rdim & 0xFFFF) * (rdim >> 16), 0)
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8), (8, 32)])
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8), (8, 32), (16, 8), (8, 16)])
 def test_binning_is_bit_exact(tile):
     sc, _ = _tiny()
     cams = [look_at((0.3, -3.6, 0.8), (0, 0, 0), 131, 97), look_at((-1.0, -3.0, 0.5), (0, 0, 0), 64, 80)]
@@ -121,7 +121,8 @@ def test_binning_bit_exact_with_boxes_over_32_tiles(tile):
 
 
 # ----------------------------------------------------------------- S6
-@pytest.mark.parametrize("tile,batch", [((16, 16), 256), ((8, 8), 64), ((32, 8), 128), ((8, 32), 96)])
+@pytest.mark.parametrize("tile,batch", [((16, 16), 256), ((8, 8), 64), ((32, 8), 128), ((8, 32), 96),
+                                        ((16, 8), 128), ((8, 16), 64)])
 def test_forward_tiny_scene_full_image(tile, batch):
     sc, cams = _tiny()
     cfg = api.GESConfig(tile_w=tile[0], tile_h=tile[1], batch=batch)
@@ -236,6 +237,8 @@ def test_tile_shapes_batches_and_persistent_are_bit_identical():
     for cfg in (api.GESConfig(sh_degree=3), api.GESConfig(sh_degree=3, tile_w=8, tile_h=8, batch=64),
                 api.GESConfig(sh_degree=3, tile_w=32, tile_h=8, batch=96),
                 api.GESConfig(sh_degree=3, tile_w=8, tile_h=32, batch=64, persistent=1),
+                api.GESConfig(sh_degree=3, tile_w=16, tile_h=8, batch=128, persistent=1),
+                api.GESConfig(sh_degree=3, tile_w=8, tile_h=16, batch=64),
                 api.GESConfig(sh_degree=3, persistent=1), api.GESConfig(sh_degree=3, batch=32, persistent=1)):
         rast, _ = H.gpu_forward(sc, cams, cfg)
         out = {k: rast.out[k].clone() for k in ("color", "depth", "alpha", "normal", "t_final", "n_contrib")}
