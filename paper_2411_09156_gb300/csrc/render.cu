@@ -101,6 +101,33 @@ __device__ __forceinline__ bool entry_ok(uint32_t e, uint32_t n_entries, uint32_
     return true;
 }
 
+// The cull vectors (u, v, a, b), (c, q_cut, beta/2, o) of record e, or zeros for no entry.
+__device__ __forceinline__ void load_cull_vectors(const float4 *rec, uint32_t e, uint32_t n_entries, uint32_t *err,
+                                                  float4 &r0, float4 &r1) {
+    r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    r1 = r0;
+    if (e == kNone || !entry_ok(e, n_entries, err)) return;
+    const float4 *r = rec + 4 * (size_t)e;
+    r0 = __ldg(r);
+    r1 = __ldg(r + 1);
+}
+
+// Tests record e (its cull vectors r0, r1 already loaded) against the warp's block and, if it can
+// contribute, stores it (with 2b in place of b) into the warp's slot `lane`.
+__device__ __forceinline__ bool cull_stage(const float4 *rec, uint32_t e, uint32_t n_entries, uint32_t *err, float4 r0,
+                                           const float4 r1, float rx0, float rx1, float ry0, float ry1,
+                                           float4 (*slot)[4], int lane) {
+    if (e == kNone || !entry_ok(e, n_entries, err)) return false;
+    if (!warp_may_hit(r0.x, r0.y, r0.z, r0.w, r1.x, r1.y * kSupportMargin, rx0, rx1, ry0, ry1)) return false;
+    const float4 *r = rec + 4 * (size_t)e;
+    r0.w = r0.w + r0.w;
+    slot[lane][0] = r0;
+    slot[lane][1] = r1;
+    slot[lane][2] = __ldg(r + 2);
+    slot[lane][3] = __ldg(r + 3);
+    return true;
+}
+
 // Loads record e, tests it against the warp's block and, if it can contribute,
 // stores it (with 2b in place of b) into the warp's slot `lane`.
 __device__ __forceinline__ bool load_cull_stage(const float4 *rec, uint32_t e, uint32_t n_entries, uint32_t *err,
@@ -147,15 +174,25 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
         float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
         uint32_t cnt = 0, last = rg.x, stop = rg.y, events = 0;
         bool done = !inside;
+        // software pipeline over 32-entry chunks: entry indices are read two chunks ahead and the
+        // cull vectors (r0, r1) of the next chunk are in flight while this chunk is evaluated
         uint32_t e_cur = entry_or_none(a.inst_entry, rg.x + lane, rg.y);
+        uint32_t e_nxt = entry_or_none(a.inst_entry, rg.x + 32 + lane, rg.y);
         uint32_t e_pf = entry_or_none(a.inst_entry, rg.x + ahead + lane, rg.y);
+        float4 q0, q1;
+        load_cull_vectors(a.rec, e_cur, a.n_entries, a.err, q0, q1);
         for (uint32_t c0 = rg.x; c0 < rg.y; c0 += 32) {
             if (__all_sync(0xffffffffu, done)) break;
             if (e_pf != kNone && entry_ok(e_pf, a.n_entries, a.err)) prefetch_l2(a.rec + 4 * (size_t)e_pf);
             e_pf = entry_or_none(a.inst_entry, c0 + 32 + ahead + lane, rg.y);
-            const uint32_t e_nxt = entry_or_none(a.inst_entry, c0 + 32 + lane, rg.y);
-            const bool hit = load_cull_stage(a.rec, e_cur, a.n_entries, a.err, rx0, rx1, ry0, ry1, slot, lane);
+            const uint32_t e_nn = entry_or_none(a.inst_entry, c0 + 64 + lane, rg.y);
+            float4 n0, n1;
+            load_cull_vectors(a.rec, e_nxt, a.n_entries, a.err, n0, n1);
+            const bool hit = cull_stage(a.rec, e_cur, a.n_entries, a.err, q0, q1, rx0, rx1, ry0, ry1, slot, lane);
             e_cur = e_nxt;
+            e_nxt = e_nn;
+            q0 = n0;
+            q1 = n1;
             uint32_t mask = __ballot_sync(0xffffffffu, hit);
             events += __popc(mask);
             __syncwarp();
