@@ -60,6 +60,9 @@ __device__ __forceinline__ uint32_t entry_or_none(const uint32_t *inst_entry, ui
 
 // Warp footprint inside a tile: 8 x 4 pixels.
 constexpr int kWarpW = 8, kWarpH = 4;
+// A staged record takes 4 float4 and is padded to 5: a quarter-warp's 16-byte stores then fall in
+// 8 distinct groups of 4 banks (lane * 5 mod 8) instead of 2 (lane * 4 mod 8).
+constexpr int kSlotVec = 5;
 
 template <int TW>
 __device__ __forceinline__ void warp_pixel(int sb, int lane, int &lx, int &ly, int &wx0, int &wy0) {
@@ -116,7 +119,7 @@ __device__ __forceinline__ void load_cull_vectors(const float4 *rec, uint32_t e,
 // contribute, stores it (with 2b in place of b) into the warp's slot `lane`.
 __device__ __forceinline__ bool cull_stage(const float4 *rec, uint32_t e, uint32_t n_entries, uint32_t *err, float4 r0,
                                            const float4 r1, float rx0, float rx1, float ry0, float ry1,
-                                           float4 (*slot)[4], int lane) {
+                                           float4 (*slot)[kSlotVec], int lane) {
     if (e == kNone || !entry_ok(e, n_entries, err)) return false;
     if (!warp_may_hit(r0.x, r0.y, r0.z, r0.w, r1.x, r1.y * kSupportMargin, rx0, rx1, ry0, ry1)) return false;
     const float4 *r = rec + 4 * (size_t)e;
@@ -131,7 +134,7 @@ __device__ __forceinline__ bool cull_stage(const float4 *rec, uint32_t e, uint32
 // Loads record e, tests it against the warp's block and, if it can contribute,
 // stores it (with 2b in place of b) into the warp's slot `lane`.
 __device__ __forceinline__ bool load_cull_stage(const float4 *rec, uint32_t e, uint32_t n_entries, uint32_t *err,
-                                                float rx0, float rx1, float ry0, float ry1, float4 (*slot)[4],
+                                                float rx0, float rx1, float ry0, float ry1, float4 (*slot)[kSlotVec],
                                                 int lane) {
     if (e == kNone || !entry_ok(e, n_entries, err)) return false;
     const float4 *r = rec + 4 * (size_t)e;
@@ -151,9 +154,9 @@ __device__ __forceinline__ bool load_cull_stage(const float4 *rec, uint32_t e, u
 template <int TW, int TH, bool DN>
 __global__ void __launch_bounds__(TW *TH) k_render_fwd(const FwdArgs a) {
     constexpr int NW = TW * TH / 32;
-    __shared__ float4 s_rec[NW][32][4];  // per-warp slot of the current chunk's records
+    __shared__ float4 s_rec[NW][32][kSlotVec];  // per-warp slot of the current chunk's records
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float4(*slot)[4] = s_rec[warp];
+    float4(*slot)[kSlotVec] = s_rec[warp];
     const uint32_t ahead = (uint32_t)a.batch;
     uint32_t tile;
     int sb;
@@ -293,10 +296,10 @@ __device__ __forceinline__ int reduce_label(int nv, int lane) {
 template <int TW, int TH, bool FULL>
 __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
     constexpr int NW = TW * TH / 32;
-    __shared__ float4 s_rec[NW][32][4];
+    __shared__ float4 s_rec[NW][32][kSlotVec];
     __shared__ uint32_t s_ent[NW][32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float4(*slot)[4] = s_rec[warp];
+    float4(*slot)[kSlotVec] = s_rec[warp];
     uint32_t *went = s_ent[warp];
     const uint32_t ahead = (uint32_t)a.batch;
     const float ln2 = 0.69314718055994531f;
