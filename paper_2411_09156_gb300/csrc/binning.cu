@@ -433,15 +433,26 @@ __global__ void k_set_count(const unsigned long long *total, uint64_t cap, uint3
     *n_inst = t >= 0xffffffffull ? 0u : (uint32_t)(t < cap ? t : cap);
 }
 
+// Tile ranges from the sorted instance keys: thread q looks at keys 4q .. 4q+3 (one 16-byte load;
+// the key buffer is capacity-sized and 256-byte aligned inside `bins`, so the load stays inside the
+// allocation; keys at n and beyond are never used) and at their neighbours 4q - 1 and 4q + 4.
 __global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t *keys, const uint32_t *n_dev, uint2 *ranges,
                                                     uint32_t n_tiles) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t n = *n_dev;
-    if (i >= n) return;
-    const uint32_t k = keys[i];
-    if (k >= n_tiles) return;
-    if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
-    if (i == n - 1 || keys[i + 1] != k) ranges[k].y = i + 1;
+    const uint32_t i0 = 4 * q;
+    if (i0 >= n) return;
+    const uint4 v = reinterpret_cast<const uint4 *>(keys)[q];
+    const uint32_t k[6] = {i0 > 0 ? keys[i0 - 1] : 0u, v.x, v.y, v.z, v.w, i0 + 4 < n ? keys[i0 + 4] : 0u};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t i = i0 + (uint32_t)j;
+        if (i >= n) break;
+        const uint32_t kk = k[j + 1];
+        if (kk >= n_tiles) continue;
+        if (i == 0 || k[j] != kk) ranges[kk].x = i;
+        if (i == n - 1 || k[j + 2] != kk) ranges[kk].y = i + 1;
+    }
 }
 
 // Longest-first tile queue: tiles are bucketed by list length on a log2 scale
@@ -518,7 +529,7 @@ cudaError_t launch_bin(const BinArgs &a, cudaStream_t s) {
     // 5. tile ranges
     e = cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)a.V.n_tiles, s);
     if (e != cudaSuccess) return e;
-    if (a.cap > 0) k_tile_ranges<<<ceil_div_u64(a.cap, 256), 256, 0, s>>>(ik[res], a.header, a.ranges, (uint32_t)a.V.n_tiles);
+    if (a.cap > 0) k_tile_ranges<<<ceil_div_u64(ceil_div_u64(a.cap, 4), 256), 256, 0, s>>>(ik[res], a.header, a.ranges, (uint32_t)a.V.n_tiles);
     // 6. longest-first queue for the persistent render
     if (a.build_queue) k_lpt_queue<<<1, 1024, 0, s>>>(a.ranges, (uint32_t)a.V.n_tiles, a.queue);
     return cudaGetLastError();
