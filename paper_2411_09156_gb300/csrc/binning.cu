@@ -403,7 +403,8 @@ __global__ void __launch_bounds__(128) k_emit(EmitArgs a) {
                         (uint32_t)((x1 >> lw) - (x0 >> lw) + 1) * (uint32_t)((y1 >> lh) - (y0 >> lh) + 1)};
     }
     uint32_t written = 0;  // hits of this lane's entry written so far
-    warp_tile_rounds(J, lane, lw, lh, tw, th,
+    __shared__ uint4 s_jobs[4][kJobWords * 32];  // 128 threads: 4 warps
+    warp_tile_rounds(J, lane, lw, lh, tw, th, s_jobs[threadIdx.x >> 5],
                      [&](uint32_t hits, uint32_t lo, uint32_t len, uint32_t, int tx, int ty, uint32_t owner,
                          bool hit) {
                          const uint32_t o_off = __shfl_sync(0xffffffffu, off, owner);

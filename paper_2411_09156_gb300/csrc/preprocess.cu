@@ -78,10 +78,10 @@ __device__ __forceinline__ void load_sh_rgb(const void *color, int st, int K, si
 // warp_tile_rounds): each lane collects its own entry's hit count and, for the
 // first 32 tests of its box, the row-major hit mask.
 __device__ __forceinline__ void warp_tile_tests(const TileJob &J, int lane, int lw, int lh, int tw, int th,
-                                                uint32_t &tiles, uint32_t &mask) {
+                                                uint4 *jobs, uint32_t &tiles, uint32_t &mask) {
     tiles = 0;
     mask = 0;
-    warp_tile_rounds(J, lane, lw, lh, tw, th,
+    warp_tile_rounds(J, lane, lw, lh, tw, th, jobs,
                      [&](uint32_t hits, uint32_t lo, uint32_t len, uint32_t first, int, int, uint32_t, bool) {
                          if (!len) return;
                          const uint32_t bits = (hits >> lo) & (len == 32u ? 0xffffffffu : ((1u << len) - 1u));
@@ -227,7 +227,8 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {
         a.rec[4 * e + 3] = r3;
     }
     uint32_t tiles, mask;
-    warp_tile_tests(J, lane, lw, lh, tw, th, tiles, mask);
+    __shared__ uint4 s_jobs[8][kJobWords * 32];  // 256 threads: 8 warps
+    warp_tile_tests(J, lane, lw, lh, tw, th, s_jobs[threadIdx.x >> 5], tiles, mask);
     unsigned long long my_tiles = 0;
     if (live) {
         const bool listed = visible && tiles > 0;
