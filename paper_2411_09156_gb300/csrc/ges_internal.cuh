@@ -237,19 +237,40 @@ struct PairEval {
     float Q, p, G, alpha_raw, alpha;
 };
 
-// Returns false if the pair is outside the support (Q > q_cut) or alpha < alpha_min.
+// Q = d^T C d of the pair (clamped at 0), d = (dx, dy), C the conic [a, b2/2; b2/2, c].
+__device__ __forceinline__ float pair_q(float dx, float dy, float a, float b2, float c) {
+    const float t = __fmaf_rn(a, dx, __fmul_rn(b2, dy));
+    return fmaxf(__fmaf_rn(__fmul_rn(c, dy), dy, __fmul_rn(dx, t)), 0.f);
+}
+
+// p = Q^(beta/2) (Q = 0 gives 0), G = exp(-p/2), alpha = min(alpha_max, o G).
+__device__ __forceinline__ void pair_alpha(float Q, float hb, float o, float alpha_max, PairEval &r) {
+    const float p = ex2_approx(__fmul_rn(hb, lg2_approx(Q)));
+    const float G = ex2_approx(__fmul_rn(kNegHalfLog2e, p));
+    const float ar = __fmul_rn(o, G);
+    r.Q = Q; r.p = p; r.G = G; r.alpha_raw = ar; r.alpha = fminf(alpha_max, ar);
+}
+
+// Returns false if the pair is outside the support (Q > q_cut) or alpha < alpha_min. A lane
+// outside the support skips the special-function work (r then holds Q only).
 __device__ __forceinline__ bool eval_pair(float dx, float dy, float a, float b2, float c, float qcut, float hb,
                                           float o, float alpha_max, float alpha_min, PairEval &r) {
-    const float t = __fmaf_rn(a, dx, __fmul_rn(b2, dy));
-    const float Q = fmaxf(__fmaf_rn(__fmul_rn(c, dy), dy, __fmul_rn(dx, t)), 0.f);
+    const float Q = pair_q(dx, dy, a, b2, c);
     r.Q = Q;
     if (Q > qcut) return false;
-    const float p = ex2_approx(__fmul_rn(hb, lg2_approx(Q)));  // Q^(beta/2); Q = 0 gives 0
-    const float G = ex2_approx(__fmul_rn(kNegHalfLog2e, p));  // exp(-p/2)
-    const float ar = __fmul_rn(o, G);
-    const float al = fminf(alpha_max, ar);
-    r.p = p; r.G = G; r.alpha_raw = ar; r.alpha = al;
-    return al >= alpha_min;
+    pair_alpha(Q, hb, o, alpha_max, r);
+    return r.alpha >= alpha_min;
+}
+
+// The same decision and values without a branch: every lane does the special-function work and
+// r is filled in full (outside the support p may be +inf and G, alpha 0; Q is finite or +inf,
+// never NaN). For a loop whose body runs on every lane of the warp anyway, where the branch
+// only adds divergence and reconvergence work.
+__device__ __forceinline__ bool eval_pair_all(float dx, float dy, float a, float b2, float c, float qcut, float hb,
+                                              float o, float alpha_max, float alpha_min, PairEval &r) {
+    const float Q = pair_q(dx, dy, a, b2, c);
+    pair_alpha(Q, hb, o, alpha_max, r);
+    return Q <= qcut && r.alpha >= alpha_min;
 }
 
 // Real spherical harmonics up to degree 3 (Condon-Shortley phase, l-major,

@@ -374,75 +374,70 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
             while (mask) {
                 const int bit = __ffs(mask) - 1;
                 mask &= mask - 1;
+                const float4 r0 = slot[bit][0], r1 = slot[bit][1];
+                const float dx = fpx - r0.x, dy = fpy - r0.y;
+                PairEval pe;
+                const bool contrib =
+                    eval_pair_all(dx, dy, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, a.alpha_max, a.alpha_min, pe) &&
+                    c0 + (uint32_t)bit < lp;
+                // Warp-uniform skip when no lane blends this splat; otherwise the body runs branch-free on
+                // every lane: a lane that does not blend takes alpha = 0, which leaves T and the running
+                // sums exactly as they were, and its values are selected to zero.
+                if (!__any_sync(0xffffffffu, contrib)) continue;
                 float g[NV];
-#pragma unroll
-                for (int q = 0; q < NV; ++q) g[q] = 0.f;
-                bool contrib = false;
-                if (c0 + (uint32_t)bit < lp) {
-                    const float4 r0 = slot[bit][0], r1 = slot[bit][1];
-                    const float dx = fpx - r0.x, dy = fpy - r0.y;
-                    PairEval pe;
-                    if (eval_pair(dx, dy, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, a.alpha_max, a.alpha_min, pe)) {
-                        contrib = true;
-                        const float4 r2 = slot[bit][2], r3 = slot[bit][3];
-                        const float al = pe.alpha;
-                        const float w = __fmul_rn(al, T);
-                        Ca0 = __fmaf_rn(w, r2.x, Ca0);
-                        Ca1 = __fmaf_rn(w, r2.y, Ca1);
-                        Ca2 = __fmaf_rn(w, r2.z, Ca2);
-                        // d out / d alpha_i = T_i sum_k g_k c_ik - (sum_k g_k (F_k - A_k) - g_alpha T_final) / (1 - alpha_i)
-                        float gc = gC0 * r2.x + gC1 * r2.y + gC2 * r2.z;
-                        float behind = gC0 * (Cf0 - Ca0) + gC1 * (Cf1 - Ca1) + gC2 * (Cf2 - Ca2);
-                        if (FULL) {
-                            Da = __fmaf_rn(w, r2.w, Da);
-                            Na0 = __fmaf_rn(w, r3.x, Na0);
-                            Na1 = __fmaf_rn(w, r3.y, Na1);
-                            Na2 = __fmaf_rn(w, r3.z, Na2);
-                            gc = gc + gD * r2.w + gN0 * r3.x + gN1 * r3.y + gN2 * r3.z;
-                            behind = behind + gD * (Df - Da) + gN0 * (Nf0 - Na0) + gN1 * (Nf1 - Na1) +
-                                     gN2 * (Nf2 - Na2);
-                        }
-                        const float dal = T * gc - (behind - gAT) * rcp_approx(1.f - al);
-                        T = __fmul_rn(T, __fsub_rn(1.f, al));
-                        const float o = r1.w, hb = r1.z;
-                        float gG = 0.f;
-                        if (pe.alpha_raw < a.alpha_max) {
-                            g[5] = dal * pe.G;
-                            gG = dal * o;
-                        }
-                        // G = exp(-p/2), p = Q^(beta/2): dG/dQ = -(beta/4) (p/Q) G, dG/dbeta = -(1/4) p ln(Q) G
-                        float gQ = 0.f;
-                        if (pe.Q > 0.f) {
-                            const float gp = gG * pe.p * pe.G;
-                            gQ = -0.5f * hb * gp * rcp_approx(pe.Q);
-                            g[6] = -0.25f * ln2 * gp * lg2_approx(pe.Q);
-                        }
-                        // Q = d^T C d with C = Sigma'^-1 and d = pixel - mean; with m = C d:
-                        // dQ/dmean = -2 m and dQ/dSigma' = -m m^T (accumulated directly:
-                        // going through the conic gradient would cancel for thin splats)
-                        const float mx = fmaf(r0.z, dx, 0.5f * r0.w * dy), my = fmaf(0.5f * r0.w, dx, r1.x * dy);
-                        const float qx = -gQ * mx, qy = -gQ * my;
-                        g[0] = 2.f * qx;
-                        g[1] = 2.f * qy;
-                        g[2] = qx * mx;
-                        g[3] = qx * my;
-                        g[4] = qy * my;
-                        constexpr int c0i = FULL ? 8 : 7;  // first colour value
-                        g[c0i] = gC0 * w;
-                        g[c0i + 1] = gC1 * w;
-                        g[c0i + 2] = gC2 * w;
-                        if (FULL) {
-                            g[7] = gD * w;
-                            g[FULL ? 11 : 0] = gN0 * w;
-                            g[FULL ? 12 : 0] = gN1 * w;
-                            g[FULL ? 13 : 0] = gN2 * w;
-                        }
+                {
+                    const float4 r2 = slot[bit][2], r3 = slot[bit][3];
+                    const float al = contrib ? pe.alpha : 0.f;  // 0: every running sum below is unchanged
+                    const float w = __fmul_rn(al, T);
+                    Ca0 = __fmaf_rn(w, r2.x, Ca0);
+                    Ca1 = __fmaf_rn(w, r2.y, Ca1);
+                    Ca2 = __fmaf_rn(w, r2.z, Ca2);
+                    // d out / d alpha_i = T_i sum_k g_k c_ik - (sum_k g_k (F_k - A_k) - g_alpha T_final) / (1 - alpha_i)
+                    float gc = gC0 * r2.x + gC1 * r2.y + gC2 * r2.z;
+                    float behind = gC0 * (Cf0 - Ca0) + gC1 * (Cf1 - Ca1) + gC2 * (Cf2 - Ca2);
+                    if (FULL) {
+                        Da = __fmaf_rn(w, r2.w, Da);
+                        Na0 = __fmaf_rn(w, r3.x, Na0);
+                        Na1 = __fmaf_rn(w, r3.y, Na1);
+                        Na2 = __fmaf_rn(w, r3.z, Na2);
+                        gc = gc + gD * r2.w + gN0 * r3.x + gN1 * r3.y + gN2 * r3.z;
+                        behind = behind + gD * (Df - Da) + gN0 * (Nf0 - Na0) + gN1 * (Nf1 - Na1) +
+                                 gN2 * (Nf2 - Na2);
+                    }
+                    const float dal = contrib ? T * gc - (behind - gAT) * rcp_approx(1.f - al) : 0.f;
+                    T = __fmul_rn(T, __fsub_rn(1.f, al));
+                    const float o = r1.w, hb = r1.z;
+                    const bool unclamped = contrib && pe.alpha_raw < a.alpha_max;
+                    g[5] = unclamped ? dal * pe.G : 0.f;
+                    const float gG = unclamped ? dal * o : 0.f;
+                    // G = exp(-p/2), p = Q^(beta/2): dG/dQ = -(beta/4) (p/Q) G, dG/dbeta = -(1/4) p ln(Q) G
+                    const bool qpos = contrib && pe.Q > 0.f;
+                    const float gp = gG * pe.p * pe.G;
+                    const float gQ = qpos ? -0.5f * hb * gp * rcp_approx(pe.Q) : 0.f;
+                    g[6] = qpos ? -0.25f * ln2 * gp * lg2_approx(pe.Q) : 0.f;
+                    // Q = d^T C d with C = Sigma'^-1 and d = pixel - mean; with m = C d:
+                    // dQ/dmean = -2 m and dQ/dSigma' = -m m^T (accumulated directly:
+                    // going through the conic gradient would cancel for thin splats)
+                    const float mx = fmaf(r0.z, dx, 0.5f * r0.w * dy), my = fmaf(0.5f * r0.w, dx, r1.x * dy);
+                    const float qx = -gQ * mx, qy = -gQ * my;
+                    g[0] = 2.f * qx;
+                    g[1] = 2.f * qy;
+                    g[2] = qx * mx;
+                    g[3] = qx * my;
+                    g[4] = qy * my;
+                    constexpr int c0i = FULL ? 8 : 7;  // first colour value
+                    g[c0i] = gC0 * w;
+                    g[c0i + 1] = gC1 * w;
+                    g[c0i + 2] = gC2 * w;
+                    if (FULL) {
+                        g[7] = gD * w;
+                        g[FULL ? 11 : 0] = gN0 * w;
+                        g[FULL ? 12 : 0] = gN1 * w;
+                        g[FULL ? 13 : 0] = gN2 * w;
                     }
                 }
-                if (__any_sync(0xffffffffu, contrib)) {
-                    const float sum = warp_reduce_n<NV>(g, lane);
-                    if (writer) atomicAdd(a.g2d + 16 * (size_t)went[bit] + gslot, sum);
-                }
+                const float sum = warp_reduce_n<NV>(g, lane);
+                if (writer) atomicAdd(a.g2d + 16 * (size_t)went[bit] + gslot, sum);
             }
             __syncwarp();
         }
