@@ -153,6 +153,11 @@ inline BinsLayout bins_layout(int32_t n, int32_t n_views, uint32_t n_tiles, uint
 }
 
 // ------------------------------------------------------------------ device helpers
+// Hint: fetch the line holding p into L2 (no value returned, no fault).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -111,6 +111,14 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {
         v = t - il * NV;
         i = (uint32_t)a.first + il;
         e = (size_t)v * a.n + i;
+        if (v == 0 && a.P.sh_degree >= 0) {
+            // the splat's colour coefficients (first and last byte: at most two lines for SH3) into
+            // L2 while the projection runs, one lane per splat
+            const int bytes = a.P.n_coeffs * 3 * (ST == 0 ? 4 : 2);
+            const char *cb = static_cast<const char *>(a.color) + (size_t)i * bytes;
+            prefetch_l2(cb);
+            prefetch_l2(cb + bytes - 1);
+        }
         const float4 po = __ldg(a.pos_op + i);
         const float4 ls = __ldg(a.lsb + i);
         const float4 q4 = __ldg(a.quat + i);

@@ -48,10 +48,6 @@ __device__ __forceinline__ int view_of_tile(const ViewSet &V, uint32_t tile) {
     return v;
 }
 
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 constexpr uint32_t kNone = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t entry_or_none(const uint32_t *inst_entry, uint32_t idx, uint32_t end) {
@@ -279,6 +275,22 @@ __device__ __forceinline__ float warp_reduce_n(float (&g)[NV], int lane) {
     return g[0] + __shfl_xor_sync(0xffffffffu, g[0], 1);
 }
 
+// warp_reduce_n<NV> with the level at offset 16 given as the values each lane keeps and sends
+// (NV even): keep[i] and send[i] are positions i and i + NV/2 in the order of the lane's half.
+template <int NV>
+__device__ __forceinline__ float warp_reduce_split(const float (&keep)[NV / 2], const float (&send)[NV / 2],
+                                                   int lane) {
+    static_assert(NV % 2 == 0 && NV >= 10 && NV <= 16, "three halvings after the split leave one value");
+    constexpr int N1 = NV / 2, N2 = (N1 + 1) / 2, N3 = (N2 + 1) / 2;
+    float g[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) g[i] = keep[i] + __shfl_xor_sync(0xffffffffu, send[i], 16);
+    halve<8, N1>(g, lane);
+    halve<4, N2>(g, lane);
+    halve<2, N3>(g, lane);
+    return g[0] + __shfl_xor_sync(0xffffffffu, g[0], 1);
+}
+
 // The value index that lane's pair holds after warp_reduce_n<NV>, or -1 (a padding zero).
 __device__ __forceinline__ int reduce_label(int nv, int lane) {
     int start = 0, valid = nv, n = nv;
@@ -303,13 +315,22 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
     uint32_t *went = s_ent[warp];
     const uint32_t ahead = (uint32_t)a.batch;
     const float ln2 = 0.69314718055994531f;
-    // the gradient values a pair contributes, packed: 0-6 mean2d, Sigma', opacity, beta; then (FULL)
-    // depth; then colour; then (FULL) normal. This lane's pair adds value `lab` into slot `gslot` of
-    // the splat's 16-float accumulator (slot 11 and, without FULL, slots 7 and 12-15 stay 0).
+    // The gradient values a pair contributes, in reduction order: the level at lane offset 16 pairs
+    // position i with i + NV/2, and the pairs are chosen so that few of them need a per-event swap
+    // (see the event body):
+    //   FULL:   mean.x  S.xx  S.xy     red    green  blue   beta  |  mean.y  S.yy  opacity  n.x  n.y  n.z  depth
+    //   colour: mean.x  S.xx  S.xy     red    blue                |  mean.y  S.yy  opacity  green  beta
+    // (S = Sigma'). Position p goes to slot (kSlots >> 4p) & 15 of the splat's 16-float
+    // accumulator: 0-1 mean, 2-4 Sigma' xx xy yy, 5 opacity, 6 beta, 7 depth, 8-10 colour,
+    // 12-14 normal (slots 11 and 15, and without FULL 7 and 12-14, stay 0). After the reduction
+    // this lane's pair holds position `lab`.
     constexpr int NV = FULL ? 14 : 10;
+    constexpr int H1 = NV / 2;
+    constexpr unsigned long long kSlots = FULL ? 0x7EDC5416A98320ull : 0x69541A8320ull;
     const int lab = reduce_label(NV, lane);
-    const int gslot = lab < 0 ? -1 : (FULL ? (lab < 11 ? lab : lab + 1) : (lab < 7 ? lab : lab + 1));
+    const int gslot = lab < 0 ? -1 : (int)((kSlots >> (4 * lab)) & 15u);
     const bool writer = (lane & 1) == 0 && gslot >= 0;
+    const bool up16 = (lane & 16) != 0;
     uint32_t tile;
     int sb;
     for (int it = 0; next_item(a.queue, a.counter, (uint32_t)a.V.n_tiles, NW, it, warp, lane, tile, sb); ++it) {
@@ -354,6 +375,13 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
                 Nf0 = a.normal[c3]; Nf1 = a.normal[c3 + P]; Nf2 = a.normal[c3 + 2 * P];
             }
         }
+        // the per-pixel factors of the channel pairs (red, n.x), (green, n.y), (blue, n.z) (FULL) or
+        // (red, green) in kept / sent order for the level at offset 16: a lane with bit 16 clear keeps
+        // the first of a pair and sends the second, the others the reverse
+        const float kc0 = FULL ? (up16 ? gN0 : gC0) : (up16 ? gC1 : gC0);
+        const float sc0 = FULL ? (up16 ? gC0 : gN0) : (up16 ? gC0 : gC1);
+        const float kc1 = up16 ? gN1 : gC1, sc1 = up16 ? gC1 : gN1;
+        const float kc2 = up16 ? gN2 : gC2, sc2 = up16 ? gC2 : gN2;
         const uint32_t wend = __reduce_max_sync(0xffffffffu, lp);  // this warp replays [rg.x, wend)
         // transmittance before splat i and the channels accumulated up to and including
         // splat i, A_k, in the forward pass's operation order: F_k - A_k, the part of the
@@ -384,7 +412,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
                 // every lane: a lane that does not blend takes alpha = 0, which leaves T and the running
                 // sums exactly as they were, and its values are selected to zero.
                 if (!__any_sync(0xffffffffu, contrib)) continue;
-                float g[NV];
+                float keep[H1], send[H1];
                 {
                     const float4 r2 = slot[bit][2], r3 = slot[bit][3];
                     const float al = contrib ? pe.alpha : 0.f;  // 0: every running sum below is unchanged
@@ -408,35 +436,38 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
                     T = __fmul_rn(T, __fsub_rn(1.f, al));
                     const float o = r1.w, hb = r1.z;
                     const bool unclamped = contrib && pe.alpha_raw < a.alpha_max;
-                    g[5] = unclamped ? dal * pe.G : 0.f;
+                    const float gop = unclamped ? dal * pe.G : 0.f;
                     const float gG = unclamped ? dal * o : 0.f;
                     // G = exp(-p/2), p = Q^(beta/2): dG/dQ = -(beta/4) (p/Q) G, dG/dbeta = -(1/4) p ln(Q) G
                     const bool qpos = contrib && pe.Q > 0.f;
                     const float gp = gG * pe.p * pe.G;
-                    const float gQ = qpos ? -0.5f * hb * gp * rcp_approx(pe.Q) : 0.f;
-                    g[6] = qpos ? -0.25f * ln2 * gp * lg2_approx(pe.Q) : 0.f;
+                    const float nq = qpos ? 0.5f * hb * gp * rcp_approx(pe.Q) : 0.f;  // -dL/dQ
+                    const float gbeta = qpos ? -0.25f * ln2 * gp * lg2_approx(pe.Q) : 0.f;
                     // Q = d^T C d with C = Sigma'^-1 and d = pixel - mean; with m = C d:
                     // dQ/dmean = -2 m and dQ/dSigma' = -m m^T (accumulated directly:
                     // going through the conic gradient would cancel for thin splats)
                     const float mx = fmaf(r0.z, dx, 0.5f * r0.w * dy), my = fmaf(0.5f * r0.w, dx, r1.x * dy);
-                    const float qx = -gQ * mx, qy = -gQ * my;
-                    g[0] = 2.f * qx;
-                    g[1] = 2.f * qy;
-                    g[2] = qx * mx;
-                    g[3] = qx * my;
-                    g[4] = qy * my;
-                    constexpr int c0i = FULL ? 8 : 7;  // first colour value
-                    g[c0i] = gC0 * w;
-                    g[c0i + 1] = gC1 * w;
-                    g[c0i + 2] = gC2 * w;
+                    // pairs (2 qx, 2 qy) and (qx mx, qy my), q = -dL/dQ m, from m in kept / sent order;
+                    // qx my = qy mx is S.xy either way. The channel pairs take their per-pixel factors
+                    // in that order already; the rest are swapped here.
+                    const float mk = up16 ? my : mx, ms = up16 ? mx : my;
+                    const float qk = nq * mk, qs = nq * ms;
+                    keep[0] = 2.f * qk; send[0] = 2.f * qs;
+                    keep[1] = qk * mk; send[1] = qs * ms;
+                    const float sxy = qk * ms;
+                    keep[2] = up16 ? gop : sxy; send[2] = up16 ? sxy : gop;
+                    keep[3] = kc0 * w; send[3] = sc0 * w;
                     if (FULL) {
-                        g[7] = gD * w;
-                        g[FULL ? 11 : 0] = gN0 * w;
-                        g[FULL ? 12 : 0] = gN1 * w;
-                        g[FULL ? 13 : 0] = gN2 * w;
+                        keep[FULL ? 4 : 0] = kc1 * w; send[FULL ? 4 : 0] = sc1 * w;
+                        keep[FULL ? 5 : 0] = kc2 * w; send[FULL ? 5 : 0] = sc2 * w;
+                        const float gdep = gD * w;
+                        keep[FULL ? 6 : 0] = up16 ? gdep : gbeta; send[FULL ? 6 : 0] = up16 ? gbeta : gdep;
+                    } else {
+                        const float cb = gC2 * w;
+                        keep[4] = up16 ? gbeta : cb; send[4] = up16 ? cb : gbeta;
                     }
                 }
-                const float sum = warp_reduce_n<NV>(g, lane);
+                const float sum = warp_reduce_split<NV>(keep, send, lane);
                 if (writer) atomicAdd(a.g2d + 16 * (size_t)went[bit] + gslot, sum);
             }
             __syncwarp();
