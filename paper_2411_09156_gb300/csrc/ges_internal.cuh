@@ -239,7 +239,7 @@ __device__ __forceinline__ void pixel_box(float u, float v, float ext_x, float e
 // Screen-space evaluation of one (pixel, splat) pair, shared by forward and
 // backward so that both take bit-identical decisions.
 struct PairEval {
-    float Q, p, G, alpha_raw, alpha;
+    float Q, lq, p, G, alpha_raw, alpha;  // lq = log2 Q
 };
 
 // Q = d^T C d of the pair (clamped at 0), d = (dx, dy), C the conic [a, b2/2; b2/2, c].
@@ -250,10 +250,11 @@ __device__ __forceinline__ float pair_q(float dx, float dy, float a, float b2, f
 
 // p = Q^(beta/2) (Q = 0 gives 0), G = exp(-p/2), alpha = min(alpha_max, o G).
 __device__ __forceinline__ void pair_alpha(float Q, float hb, float o, float alpha_max, PairEval &r) {
-    const float p = ex2_approx(__fmul_rn(hb, lg2_approx(Q)));
+    const float lq = lg2_approx(Q);
+    const float p = ex2_approx(__fmul_rn(hb, lq));
     const float G = ex2_approx(__fmul_rn(kNegHalfLog2e, p));
     const float ar = __fmul_rn(o, G);
-    r.Q = Q; r.p = p; r.G = G; r.alpha_raw = ar; r.alpha = fminf(alpha_max, ar);
+    r.Q = Q; r.lq = lq; r.p = p; r.G = G; r.alpha_raw = ar; r.alpha = fminf(alpha_max, ar);
 }
 
 // Returns false if the pair is outside the support (Q > q_cut) or alpha < alpha_min. A lane
@@ -478,6 +479,9 @@ struct BwdArgs {
 cudaError_t launch_preprocess(const PreArgs &a, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t s);
 cudaError_t launch_bin(const BinArgs &a, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs on bits [0, bits), 8 bits a pass (binning.cu).
+cudaError_t radix_sort(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, const uint32_t *n_dev,
+                       uint32_t n_host_max, int bits, uint32_t *hist, uint32_t *partials, cudaStream_t s);
 cudaError_t launch_render_fwd(const FwdArgs &a, cudaStream_t s);
 cudaError_t launch_render_bwd(const BwdArgs &a, cudaStream_t s);
 bool tile_shape_supported(int tw, int th);

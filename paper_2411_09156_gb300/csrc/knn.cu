@@ -19,9 +19,6 @@
 
 namespace ges {
 
-cudaError_t radix_sort(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, const uint32_t *n_dev,
-                       uint32_t n_host_max, int bits, uint32_t *hist, uint32_t *partials, cudaStream_t s);
-
 namespace {
 
 constexpr int kK = GES_KNN_K;

@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_bwd(const BwdArgs a) {
                     const bool qpos = contrib && pe.Q > 0.f;
                     const float gp = gG * pe.p * pe.G;
                     const float nq = qpos ? 0.5f * hb * gp * rcp_approx(pe.Q) : 0.f;  // -dL/dQ
-                    const float gbeta = qpos ? -0.25f * ln2 * gp * lg2_approx(pe.Q) : 0.f;
+                    const float gbeta = qpos ? -0.25f * ln2 * gp * pe.lq : 0.f;
                     // Q = d^T C d with C = Sigma'^-1 and d = pixel - mean; with m = C d:
                     // dQ/dmean = -2 m and dQ/dSigma' = -m m^T (accumulated directly:
                     // going through the conic gradient would cancel for thin splats)
