@@ -272,20 +272,37 @@ __device__ __forceinline__ float seg_sum(float x, int width) {
     return x;
 }
 
-// Recursive-halving sum of 48 values over a segment of SEG lanes (compile-time
-// sizes keep every index static, so the values stay in registers): at each level a
-// lane keeps half of its values and adds its partner's copy of them, so 48 values
-// cost 24 + 12 + ... shuffles instead of 48 per level. 48 = 3 x 16 halves four
-// times; with 32 lanes the fifth level adds the 3 remaining values outright and
-// the even lane of each pair writes. Lane v writes the sums it holds, values
-// [base, base + CNT), that exist (index < 3K).
+// Recursive-halving sum of the 48 values wc_c Y_k (value 3k + c) over a segment of SEG lanes
+// (compile-time sizes keep every index static, so the values stay in registers): at each level
+// a lane keeps half of its values and adds its partner's copy of them, so 48 values cost
+// 24 + 12 + ... shuffles instead of 48 per level. 48 = 3 x 16 halves four times; with 32 lanes
+// the fifth level adds the 3 remaining values outright and the even lane of each pair writes.
+// Lane v writes the sums it holds, values [base, base + CNT), that exist (index < 3K). At the
+// first level value 3k + c pairs with 3(k + 8) + c, both wc_c times a basis value, so the lane
+// takes Y_k and Y_k+8 in kept / sent order (16 selects) instead of swapping 24 product pairs.
 template <int SEG>
-__device__ __forceinline__ void write_sh_grad(float (&t)[48], int v, int K, bool ok, float *gcol) {
+__device__ __forceinline__ void write_sh_grad(const float (&wc)[3], const float (&Y)[16], int v, int K, bool ok,
+                                              float *gcol) {
     constexpr int HALVINGS = SEG >= 16 ? 4 : (SEG == 8 ? 3 : (SEG == 4 ? 2 : (SEG == 2 ? 1 : 0)));
     constexpr int CNT = 48 >> HALVINGS;
+    float t[48];
     int base = 0;
+    if (HALVINGS == 0) {
 #pragma unroll
-    for (int l = 0, o = SEG >> 1, cnt = 48; l < HALVINGS; ++l, o >>= 1, cnt >>= 1) {
+        for (int k = 0; k < 16; ++k) { t[3 * k] = wc[0] * Y[k]; t[3 * k + 1] = wc[1] * Y[k]; t[3 * k + 2] = wc[2] * Y[k]; }
+    } else {
+        constexpr int o = SEG >> 1;
+        const bool up = (v & o) != 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float yk = up ? Y[k + 8] : Y[k], ys = up ? Y[k] : Y[k + 8];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) t[3 * k + c] = wc[c] * yk + __shfl_xor_sync(0xffffffffu, wc[c] * ys, o);
+        }
+        if (up) base += 24;
+    }
+#pragma unroll
+    for (int l = 1, o = SEG >> 2, cnt = 24; l < HALVINGS; ++l, o >>= 1, cnt >>= 1) {
         const int h = cnt >> 1;
         const bool up = (v & o) != 0;
 #pragma unroll
@@ -529,10 +546,7 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(PreBwdArgs a) {
     for (int k = 0; k < 16; ++k) Y[k] = 0.f;
     if (has) sh_eval(a.P.sh_degree, sdir[0], sdir[1], sdir[2], Y);
     // the 48 products wc_c Y_k summed over the segment's lanes
-    float t[48];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) { t[3 * k] = wc[0] * Y[k]; t[3 * k + 1] = wc[1] * Y[k]; t[3 * k + 2] = wc[2] * Y[k]; }
-    write_sh_grad<SEG>(t, v, K, splat_ok, a.g_color + (size_t)i * K * 3);
+    write_sh_grad<SEG>(wc, Y, v, K, splat_ok, a.g_color + (size_t)i * K * 3);
 }
 
 cudaError_t launch_preprocess(const PreArgs &a, cudaStream_t s) {
