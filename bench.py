@@ -279,13 +279,14 @@ def host_link_gbs(nbytes: int = 1 << 29) -> dict:
 
 
 def other_workloads(cfg, args, flush, rank: int, world: int) -> dict:
-    """fwd+bwd Mpixel/s of the other workloads with the main line's tile shape and prefetch
-    distance, timed like the main line (graphed steps, L2 flushed, random upstream gradients):
-    the 1k-splat 128x128 view, the 100k-splat 800x800 view, the 1.5M-splat 1600x1040 view, and the
-    3M-splat 16-view batch both batched and as 16 sequential one-view steps."""
+    """fwd+bwd Mpixel/s of the other workloads, timed like the main line (graphed steps, L2
+    flushed, random upstream gradients): the 1k-splat 128x128 view, the 100k-splat 800x800 view,
+    the 1.5M-splat 1600x1040 view, and the 3M-splat 16-view batch both batched and as 16
+    sequential one-view steps. Each workload gets its own autotuned tile shape and prefetch
+    distance, as the main line does (the main line's with --no-autotune, --tile or --batch)."""
     import torch
     from paper_2411_09156_gb300 import api
-    from paper_2411_09156_gb300.batch import BatchPlan
+    from paper_2411_09156_gb300.batch import BatchPlan, autotune
     out = {}
     for name in ("tiny-1k-128", "object-100k-800", "scene-1.5M-1600x1040", "drt16-3M"):
         sc, cams = make_workload(name, rank)
@@ -293,11 +294,14 @@ def other_workloads(cfg, args, flush, rank: int, world: int) -> dict:
         P = sum(c.width * c.height for c in cams)
         ups = upstream_grads(P, 4000 + rank)
         c = dataclasses.replace(cfg, sh_degree=sc.sh_degree)
+        if not (args.no_autotune or args.tile or args.batch):
+            c = autotune(sc.n, cams, c, inputs, ups, key=name)
         plan = BatchPlan(sc.n, cams, c, inputs, ups)
         ms = timed_call(plan.step, args.warmup, args.steps, flush, world)
         plan.check()
         rec = {"value": world * P / (ms / 1e3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ms, "splats": sc.n,
-               "views": len(cams), "pixels": P, "gpu_launches": plan.launches_per_step() * args.steps}
+               "views": len(cams), "pixels": P, "tile": [c.tile_w, c.tile_h], "batch": c.batch,
+               "gpu_launches": plan.launches_per_step() * args.steps}
         del plan
         if len(cams) > 1:
             pv_cfg = c.replace(persistent=0)
