@@ -93,7 +93,7 @@ __device__ __forceinline__ void warp_tile_tests(const TileJob &J, int lane, int 
 // ST: the colour storage (Params::color_storage), a template parameter so that each storage
 // gets its own register allocation.
 template <int ST>
-__global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {
+__global__ void __launch_bounds__(32, 32) k_preprocess(PreArgs a) {
     const uint32_t NV = (uint32_t)a.V.n_views;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;  // n * NV < 2^31 (host check)
     const int lane = threadIdx.x & 31;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {
         a.rec[4 * e + 3] = r3;
     }
     uint32_t tiles, mask;
-    __shared__ uint4 s_jobs[8][kJobWords * 32];  // 256 threads: 8 warps
+    __shared__ uint4 s_jobs[1][kJobWords * 32];  // 32 threads: 1 warp
     warp_tile_tests(J, lane, lw, lh, tw, th, s_jobs[threadIdx.x >> 5], tiles, mask);
     unsigned long long my_tiles = 0;
     if (live) {
@@ -245,18 +245,11 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(PreArgs a) {
         a.binrec[2 * e + 1] = make_uint4(mask, rect, rdim, 0u);
         my_tiles = listed ? tiles : 0u;
     }
-    // block reduction of the tile count, one atomic per CTA
-    __shared__ unsigned long long s_sum[8];
+    // tile count: a warp sum, one atomic per warp (a CTA is one warp)
     unsigned long long tsum = my_tiles;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) tsum += __shfl_down_sync(0xffffffffu, tsum, off);
-    if (lane == 0) s_sum[threadIdx.x >> 5] = tsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long sum = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += s_sum[w];
-        if (sum) atomicAdd(a.total, sum);
-    }
+    if (lane == 0 && tsum) atomicAdd(a.total, tsum);
 }
 
 // ---------------------------------------------------------------------------
@@ -331,7 +324,7 @@ __device__ __forceinline__ void write_sh_grad(const float (&wc)[3], const float 
 // writes the geometry gradients; the SH coefficient gradients are written by all
 // lanes of the segment, coefficient k by lane k mod seg.
 template <int SEG>
-__global__ void __launch_bounds__(256, 3) k_preprocess_bwd(PreBwdArgs a) {
+__global__ void __launch_bounds__(32, 28) k_preprocess_bwd(PreBwdArgs a) {
     const int NV = a.V.n_views;
     constexpr int seg = SEG;  // lanes per splat: the view count rounded up to a power of two
     const int lane = threadIdx.x & 31;
@@ -552,10 +545,12 @@ __global__ void __launch_bounds__(256, 3) k_preprocess_bwd(PreBwdArgs a) {
 cudaError_t launch_preprocess(const PreArgs &a, cudaStream_t s) {
     if (a.count <= 0) return cudaSuccess;
     const long long threads = (long long)a.count * a.V.n_views;
-    const unsigned grid = (unsigned)((threads + 255) / 256);
-    if (a.P.color_storage == 1) k_preprocess<1><<<grid, 256, 0, s>>>(a);
-    else if (a.P.color_storage == 2) k_preprocess<2><<<grid, 256, 0, s>>>(a);
-    else k_preprocess<0><<<grid, 256, 0, s>>>(a);
+    // one warp per CTA: the warps share nothing but the SM, so a warp whose tile tests end early
+    // frees its slot at once (0.93 -> 0.83 ms against CTAs of 8 warps)
+    const unsigned grid = (unsigned)((threads + 31) / 32);
+    if (a.P.color_storage == 1) k_preprocess<1><<<grid, 32, 0, s>>>(a);
+    else if (a.P.color_storage == 2) k_preprocess<2><<<grid, 32, 0, s>>>(a);
+    else k_preprocess<0><<<grid, 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -564,15 +559,17 @@ cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t s) {
     int seg = 1;
     while (seg < a.V.n_views) seg <<= 1;
     const long long warps = ((long long)a.count + (32 / seg) - 1) / (32 / seg);
-    const size_t smem = a.P.sh_degree >= 0 ? (size_t)8 * (32 / seg) * a.P.n_coeffs * 3 * sizeof(float) : 0;
-    const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+    // one warp per CTA, 28 resident per SM (72 registers: more resident warps hide the
+    // loads better than the few spills cost; 0.85 -> 0.75 ms against CTAs of 8 warps)
+    const size_t smem = a.P.sh_degree >= 0 ? (size_t)(32 / seg) * a.P.n_coeffs * 3 * sizeof(float) : 0;
+    const unsigned grid = (unsigned)warps;
     switch (seg) {
-        case 1: k_preprocess_bwd<1><<<grid, 256, smem, s>>>(a); break;
-        case 2: k_preprocess_bwd<2><<<grid, 256, smem, s>>>(a); break;
-        case 4: k_preprocess_bwd<4><<<grid, 256, smem, s>>>(a); break;
-        case 8: k_preprocess_bwd<8><<<grid, 256, smem, s>>>(a); break;
-        case 16: k_preprocess_bwd<16><<<grid, 256, smem, s>>>(a); break;
-        default: k_preprocess_bwd<32><<<grid, 256, smem, s>>>(a); break;
+        case 1: k_preprocess_bwd<1><<<grid, 32, smem, s>>>(a); break;
+        case 2: k_preprocess_bwd<2><<<grid, 32, smem, s>>>(a); break;
+        case 4: k_preprocess_bwd<4><<<grid, 32, smem, s>>>(a); break;
+        case 8: k_preprocess_bwd<8><<<grid, 32, smem, s>>>(a); break;
+        case 16: k_preprocess_bwd<16><<<grid, 32, smem, s>>>(a); break;
+        default: k_preprocess_bwd<32><<<grid, 32, smem, s>>>(a); break;
     }
     return cudaGetLastError();
 }
