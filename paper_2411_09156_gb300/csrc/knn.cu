@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(256) k_knn_point_keys(const float4 *pts, int m
 
 // Queries at arbitrary points, taken in cell order (order[r]: the r-th query by cell), so a
 // warp searches one neighbourhood; w = 0: no query, the list is all -1.
-__global__ void __launch_bounds__(128) k_knn_points(const float4 *spos, const uint2 *ranges, const uint32_t *bcount,
+__global__ void __launch_bounds__(32) k_knn_points(const float4 *spos, const uint2 *ranges, const uint32_t *bcount,
                                                     const KnnGrid *gp, const float4 *pts, const uint32_t *order, int m,
                                                     int32_t *knn) {
     const int r0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -491,7 +491,9 @@ cudaError_t knn_points_run(int32_t n, const float4 *pos, int32_t m, const float4
                    at<uint32_t>(qws, Q.partials), s);
     if (e != cudaSuccess) return e;
     const int res = ((Q.bits + 7) / 8) & 1;
-    k_knn_points<<<ceil_div_u64(m, 128), 128, 0, s>>>(at<float4>(workspace, L.spos), at<uint2>(workspace, L.ranges),
+    // one warp per CTA: query walks differ widely in length, and a CTA of several warps would hold
+    // its slot until its longest walk ended
+    k_knn_points<<<ceil_div_u64(m, 32), 32, 0, s>>>(at<float4>(workspace, L.spos), at<uint2>(workspace, L.ranges),
                                                      at<uint32_t>(workspace, L.bcount), at<KnnGrid>(workspace, L.grid),
                                                      pts, vals[res], m, knn);
     return cudaGetLastError();

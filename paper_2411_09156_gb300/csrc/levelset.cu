@@ -24,7 +24,9 @@ cudaError_t knn_points_run(int32_t n, const float4 *pos, int32_t m, const float4
 namespace {
 
 constexpr int kK = GES_KNN_K;
-constexpr int kLsThreads = 128;
+// one warp per CTA: marches differ in length, and a CTA of several warps would hold its slot
+// until its longest march ended
+constexpr int kLsThreads = 32;
 constexpr int kLsChunk = 16;  // march samples whose densities a thread holds at once
 constexpr float kHalfLog2e = 0.72134752044448170f;
 
