@@ -317,6 +317,15 @@ __device__ __forceinline__ void write_sh_grad(const float (&wc)[3], const float 
     }
 }
 
+// Per-splat stride (floats) of the staged SH coefficients: the 3K floats rounded up to whole
+// float4s, an odd number of them, so that the staged splats of a warp start in distinct bank
+// groups (a stride of 48 floats put every other splat on the same banks).
+__host__ __device__ __forceinline__ int sh_stage_stride(int K) {
+    int s4 = (K * 3 + 3) / 4;
+    if ((s4 & 1) == 0) ++s4;
+    return 4 * s4;
+}
+
 // One lane per (splat, view): the lanes of a splat are adjacent (a segment of
 // `seg` lanes, the view count rounded up to a power of two), each lane takes its
 // view's screen-space gradient back through S1-S4, and the per-splat sums over
@@ -341,25 +350,37 @@ __global__ void __launch_bounds__(32, 28) k_preprocess_bwd(PreBwdArgs a) {
     // (dynamic shared memory: spw * K * 3 floats per warp)
     extern __shared__ float s_sh[];
     const int K = a.P.n_coeffs;
-    float *wsh = s_sh + (threadIdx.x >> 5) * (spw * K * 3);
+    const int S = sh_stage_stride(K), K3 = K * 3;
+    float *wsh = s_sh + (threadIdx.x >> 5) * (spw * S);
     if (a.P.sh_degree >= 0) {
         const long long first = a.first + gw * spw;
         const int nsp = (int)min((long long)spw, end - first);
         const int nflt = nsp * K * 3;
         const int st = a.P.color_storage;
         const size_t off = (size_t)first * K * 3;
-        if (st == 0 && (K * 3) % 4 == 0) {
+        // flat float f of the run goes to splat f / 3K, offset f % 3K (a float4 or a 16-byte chunk
+        // of 16-bit values never straddles two splats on those paths)
+        if (st == 0 && K3 % 4 == 0) {
             const float4 *s4 = reinterpret_cast<const float4 *>(static_cast<const float *>(a.color) + off);
-            for (int q = lane; q < nflt / 4; q += 32) reinterpret_cast<float4 *>(wsh)[q] = __ldg(s4 + q);
-        } else if (st != 0 && (K * 3) % 8 == 0) {
+            for (int q = lane; q < nflt / 4; q += 32) {
+                const int sp = 4 * q / K3;
+                *reinterpret_cast<float4 *>(wsh + sp * S + (4 * q - sp * K3)) = __ldg(s4 + q);
+            }
+        } else if (st != 0 && K3 % 8 == 0) {
             const char *s16 = static_cast<const char *>(a.color) + 2 * off;
-            for (int q = lane; q < nflt / 8; q += 32) ld_color8(s16 + 16 * q, st, wsh + 8 * q);
+            for (int q = lane; q < nflt / 8; q += 32) {
+                const int sp = 8 * q / K3;
+                ld_color8(s16 + 16 * q, st, wsh + sp * S + (8 * q - sp * K3));
+            }
         } else {
-            for (int q = lane; q < nflt; q += 32) wsh[q] = ld_color(a.color, st, off + q);
+            for (int q = lane; q < nflt; q += 32) {
+                const int sp = q / K3;
+                wsh[sp * S + (q - sp * K3)] = ld_color(a.color, st, off + q);
+            }
         }
         __syncwarp();
     }
-    const float *cf = wsh + (lane / seg) * K * 3;  // this lane's splat
+    const float *cf = wsh + (lane / seg) * S;  // this lane's splat
     const float4 po = __ldg(a.pos_op + i);
     const float4 ls = __ldg(a.lsb + i);
     const float4 q4 = __ldg(a.quat + i);
@@ -561,7 +582,7 @@ cudaError_t launch_preprocess_bwd(const PreBwdArgs &a, cudaStream_t s) {
     const long long warps = ((long long)a.count + (32 / seg) - 1) / (32 / seg);
     // one warp per CTA, 28 resident per SM (72 registers: more resident warps hide the
     // loads better than the few spills cost; 0.85 -> 0.75 ms against CTAs of 8 warps)
-    const size_t smem = a.P.sh_degree >= 0 ? (size_t)(32 / seg) * a.P.n_coeffs * 3 * sizeof(float) : 0;
+    const size_t smem = a.P.sh_degree >= 0 ? (size_t)(32 / seg) * sh_stage_stride(a.P.n_coeffs) * sizeof(float) : 0;
     const unsigned grid = (unsigned)warps;
     switch (seg) {
         case 1: k_preprocess_bwd<1><<<grid, 32, smem, s>>>(a); break;
