@@ -28,7 +28,10 @@ constexpr int kB = kLT + 2 * kR;      // 42: statistics region
 constexpr int kLossThreads = 384;
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
-constexpr size_t kLossSmem = sizeof(float) * (2 * kA * kA + 5 * kA * kB + 3 * kB * kB);
+// row stride of the row-filtered products: 55 = 7 (mod 16) puts the 32 lanes of a column-pass read
+// (consecutive columns, wrapping into the rows 6 below) on 32 distinct banks
+constexpr int kBP = 55;
+constexpr size_t kLossSmem = sizeof(float) * (2 * kA * kA + 5 * kA * kBP + 3 * kB * kB);
 static_assert(kB % 6 == 0 && kLT % 4 == 0, "register blocking of the filter passes");
 
 struct LossArgs {
@@ -49,8 +52,8 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const LossArgs a) {
     extern __shared__ float sm[];
     float *sx = sm;                // [kA][kA]
     float *sy = sx + kA * kA;      // [kA][kA]
-    float *h1 = sy + kA * kA;      // [5][kA][kB]: row-filtered products
-    float *st = h1 + 5 * kA * kB;  // [3][kB][kB]: SSIM derivatives on the statistics region
+    float *h1 = sy + kA * kA;       // [5][kA][kBP]: row-filtered products (kB used per row)
+    float *st = h1 + 5 * kA * kBP;  // [3][kB][kB]: SSIM derivatives on the statistics region
     float *h2 = h1;                // [3][kB][kLT]: row-filtered derivatives (reuses h1)
     const int tid = threadIdx.x;
     const int b = blockIdx.x;
@@ -93,12 +96,12 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const LossArgs a) {
                     m3 = fmaf(wy, yv[o + k], m3);
                     m4 = fmaf(wx, yv[o + k], m4);
                 }
-                const int j = ry * kB + c0 + o;
+                const int j = ry * kBP + c0 + o;
                 h1[j] = m0;
-                h1[kA * kB + j] = m1;
-                h1[2 * kA * kB + j] = m2;
-                h1[3 * kA * kB + j] = m3;
-                h1[4 * kA * kB + j] = m4;
+                h1[kA * kBP + j] = m1;
+                h1[2 * kA * kBP + j] = m2;
+                h1[3 * kA * kBP + j] = m3;
+                h1[4 * kA * kBP + j] = m4;
             }
         }
         __syncthreads();
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const LossArgs a) {
             for (int q = 0; q < 5; ++q) {
                 float col[16];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) col[k] = h1[q * kA * kB + (r0 + k) * kB + cx];
+                for (int k = 0; k < 16; ++k) col[k] = h1[q * kA * kBP + (r0 + k) * kBP + cx];
 #pragma unroll
                 for (int o = 0; o < 6; ++o) {
                     float m = 0.f;
